@@ -1,0 +1,218 @@
+"""Pins for the oracle's ray generation and ray casting (Sec. 2.2).
+
+* Philox: the shared round structure is checked bit-for-bit against
+  numpy's independent Philox-4x64-10; the 4x32 outputs are checked for
+  uniformity and avalanche.
+* Directions: unit length, uniform on the sphere (moments; Archimedes: the
+  z component is uniform on [-1, 1]).
+* Ray/triangle: hand-derived hits, and agreement with an fp64 ray-plane +
+  barycentric computation on random cases.
+* Closest hit + minimum over rays: the distribution law of the minimum over
+  R uniform rays above a plane, P(min <= d0/u) = 1 - ((1+u)/2)^R; the
+  front/back convention; and "traced minimum >= exact distance".
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import scenes as S
+
+BMIN = np.zeros(3, np.float32)
+
+
+def test_philox_structure_matches_numpy_4x64():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        ctr = rng.integers(0, 2 ** 63, 4, dtype=np.uint64)
+        key = rng.integers(0, 2 ** 63, 2, dtype=np.uint64)
+        bg = np.random.Philox(counter=ctr, key=key)
+        ref = bg.random_raw(4).astype(np.uint64)
+        # numpy increments the counter before each block
+        c1 = ctr.copy()
+        c1[0] += np.uint64(1)
+        assert np.array_equal(oracle.philox4x64(c1, key), ref)
+
+
+def test_philox4x32_statistics():
+    outs = np.array([oracle.philox4x32([i, 7, 0, 0], [1234, 5678]) for i in range(20000)])
+    bits = np.unpackbits(outs.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.002
+    by = outs.view(np.uint8).ravel()
+    hist = np.bincount(by, minlength=256)
+    exp = by.size / 256
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    assert chi2 < 255 + 5 * math.sqrt(2 * 255)
+    # avalanche: flipping one counter bit flips ~half the output bits
+    flips = []
+    for b in range(32):
+        a = oracle.philox4x32([5, 6, 7, 8], [9, 10])
+        c = oracle.philox4x32([5 ^ (1 << b), 6, 7, 8], [9, 10])
+        flips.append(np.unpackbits((a ^ c).view(np.uint8)).sum())
+    assert 50 < np.mean(flips) < 78
+    # key sensitivity
+    assert not np.array_equal(oracle.philox4x32([1, 2, 3, 4], [0, 0]), oracle.philox4x32([1, 2, 3, 4], [0, 1]))
+
+
+def _dirs(n, seed=11):
+    return np.array([oracle.sphere_dir(seed, i // 64, 3, i % 64)[0] for i in range(n)], np.float64)
+
+
+def test_directions_uniform_on_sphere():
+    n = 60000
+    d = _dirs(n)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-6)
+    sig = 1 / math.sqrt(3 * n)
+    assert np.all(np.abs(d.mean(0)) < 5 * sig)
+    cov = d.T @ d / n
+    assert np.allclose(cov, np.eye(3) / 3, atol=6 / math.sqrt(n))
+    # Archimedes: each coordinate is uniform on [-1, 1]; KS test on z and x
+    for k in (0, 2):
+        z = np.sort(d[:, k])
+        ecdf = np.arange(1, n + 1) / n
+        ks = np.max(np.abs(ecdf - (z + 1) / 2))
+        assert ks < 1.8 / math.sqrt(n)
+
+
+def test_direction_is_a_function_of_its_counter():
+    a, _ = oracle.sphere_dir(5, 100, 2, 7)
+    b, _ = oracle.sphere_dir(5, 100, 2, 7)
+    assert np.array_equal(a, b)
+    others = [oracle.sphere_dir(5, 101, 2, 7)[0], oracle.sphere_dir(5, 100, 3, 7)[0],
+              oracle.sphere_dir(5, 100, 2, 8)[0], oracle.sphere_dir(6, 100, 2, 7)[0]]
+    for o in others:
+        assert not np.array_equal(a, o)
+
+
+def test_ray_triangle_closed_forms():
+    v0, v1, v2 = [0, 0, 0], [1, 0, 0], [0, 1, 0]      # normal +z
+    hit, t, front = oracle.ray_triangle([0.25, 0.25, 1], [0, 0, -1], v0, v1, v2)
+    assert hit and t == 1.0 and front
+    hit, t, front = oracle.ray_triangle([0.25, 0.25, -2], [0, 0, 1], v0, v1, v2)
+    assert hit and t == 2.0 and not front
+    # vertex and edge are part of the closed triangle
+    assert oracle.ray_triangle([0, 0, 1], [0, 0, -1], v0, v1, v2)[0]
+    assert oracle.ray_triangle([0.5, 0.5, 1], [0, 0, -1], v0, v1, v2)[0]
+    # outside, parallel, behind
+    assert not oracle.ray_triangle([0.75, 0.75, 1], [0, 0, -1], v0, v1, v2)[0]
+    assert not oracle.ray_triangle([0.25, 0.25, 1], [1, 0, 0], v0, v1, v2)[0]
+    assert not oracle.ray_triangle([0.25, 0.25, 1], [0, 0, 1], v0, v1, v2)[0]
+    # origin on the surface: t = 0 counts
+    hit, t, _ = oracle.ray_triangle([0.25, 0.25, 0], [0, 0, 1], v0, v1, v2)
+    assert hit and t == 0.0
+
+
+def test_ray_triangle_matches_fp64_plane_intersection():
+    rng = np.random.default_rng(3)
+    agree = 0
+    for _ in range(4000):
+        tri = rng.uniform(-1, 1, (3, 3)).astype(np.float32)
+        o = rng.uniform(-2, 2, 3).astype(np.float32)
+        target = (tri.T @ rng.dirichlet([1, 1, 1]) + rng.normal(0, 0.3, 3))
+        d = (target - o)
+        d = (d / np.linalg.norm(d)).astype(np.float32)
+        hit, t, front = oracle.ray_triangle(o, d, *tri)
+        a, b, c = tri.astype(np.float64)
+        n = np.cross(b - a, c - a)
+        dd, oo = d.astype(np.float64), o.astype(np.float64)
+        den = n @ dd
+        if abs(den) < 1e-6:
+            continue
+        t64 = n @ (a - oo) / den
+        p = oo + t64 * dd
+        # barycentrics by sub-areas
+        area = np.linalg.norm(n)
+        w1 = np.dot(np.cross(p - a, c - a), n) / area ** 2
+        w2 = np.dot(np.cross(b - a, p - a), n) / area ** 2
+        w0 = 1 - w1 - w2
+        margin = min(w0, w1, w2)
+        if t64 > 1e-4 and margin > 1e-4:
+            assert hit and abs(t - t64) <= 1e-5 * max(1.0, t64)
+            assert front == (den < 0)
+            agree += 1
+        elif t64 < -1e-4 or margin < -1e-4:
+            assert not hit
+    assert agree > 500
+
+
+def test_min_over_rays_plane_law():
+    # Floor only (huge quad at y = 0, normal +y); texel j at height d0 =
+    # (jy + 0.5) h.  U = d0 / r_min has CDF ((1+u)/2)^R on [0, 1].
+    R, nf = 8, 64
+    v = np.array([[-1e3, 0, -1e3], [-1e3, 0, 1e3], [1e3, 0, 1e3], [1e3, 0, -1e3]], np.float32)
+    t = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    rng = np.random.default_rng(1)
+    jx, jz = rng.integers(0, nf, 3000), rng.integers(0, nf, 3000)
+    jy = rng.integers(0, 8, 3000)
+    tex = jx + nf * (jy + nf * jz)
+    tex = np.unique(tex)
+    r, cf, cb, _ = oracle.trace(v, t, BMIN, 1.0, nf, 99, 0, R, tex)
+    d0 = ((tex // nf) % nf + 0.5) / nf
+    U = np.where(np.isfinite(r), d0 / r, 0.0)
+    U = np.sort(np.minimum(U, 1.0))
+    n = U.size
+    F = ((1 + U) / 2) ** R
+    ks = max(np.max(np.arange(1, n + 1) / n - F), np.max(F - np.arange(0, n) / n))
+    assert ks < 1.63 / math.sqrt(n)      # 1 % critical value
+    # every hit is a front hit (rays come from above the upward floor)
+    assert np.all(cb == 0) and cf.sum() > 0
+    # from below the floor every hit is a back hit
+    vb = v.copy()
+    vb[:, 1] = 0.9
+    r2, cf2, cb2, _ = oracle.trace(vb, t, BMIN, 1.0, nf, 99, 0, R, tex)
+    assert np.all(cf2 == 0) and cb2.sum() > 0
+
+
+def test_inside_box_back_hits_and_lower_bound():
+    m = S.merge([S.box_mesh((0.5, 0.5, 0.5), 0.3)])
+    nf = 32
+    j = np.arange(nf ** 3)
+    cen = (np.stack([j % nf, (j // nf) % nf, j // (nf * nf)], 1) + 0.5) / nf
+    inside = np.all(np.abs(cen - 0.5) < 0.29, axis=1)
+    tex = np.random.default_rng(2).choice(np.nonzero(inside)[0], 400, replace=False)
+    r, cf, cb, _ = oracle.trace(m.verts, m.tris, BMIN, 1.0, nf, 5, 0, 16, tex)
+    assert np.all(cf == 0) and np.all(cb == 16)     # every ray escapes through a back face
+    d = oracle.point_mesh_distance(m.verts, m.tris, cen[tex])
+    assert np.all(r >= d - 1e-6)
+
+
+def test_traced_minimum_bounds_and_convergence():
+    m = S.tiny_scene()
+    nc, nf = 16, 32
+    occ = oracle.voxelize(m.verts, m.tris, BMIN, 1.0, nc)
+    seeds, _ = oracle.jfa(occ, nc)
+    c = oracle.coarse_sdf(seeds, nc, 1.0, 0.5)
+    mask, _ = oracle.mask_fill(seeds, nc, 2.0, 0.5, c)
+    tex = np.random.default_rng(4).choice(np.nonzero(mask)[0], 300, replace=False)
+    cen = oracle.texel_centres(BMIN, 1.0, nf, tex).astype(np.float64)
+    d = oracle.point_mesh_distance(m.verts, m.tris, cen)
+    u = np.full(tex.size, np.inf)
+    med = []
+    for frame in range(16):
+        r, *_ = oracle.trace(m.verts, m.tris, BMIN, 1.0, nf, 0, frame, 16, tex)
+        un = oracle.eq1_update(u, 0.0, r, 1.0)
+        assert np.all(un <= u)                      # non-increasing (alpha = 1)
+        u = un
+        fin = np.isfinite(u)
+        assert np.all(u[fin] >= d[fin] - 1e-6)      # never below the true distance
+        if frame in (0, 3, 15):
+            med.append(np.median((u[fin] - d[fin]) / np.maximum(d[fin], 1e-3)))
+    assert med[0] > med[1] > med[2]
+
+
+def test_eq1_and_sign_and_reset_rules():
+    u = np.array([np.inf, 0.3, 0.3, np.inf])
+    c = np.array([0.1, 0.1, -0.02, 0.2])
+    r = np.array([0.5, 0.2, np.inf, np.inf])
+    assert np.array_equal(oracle.eq1_update(u, c, r, 1.0), [0.5, 0.2, 0.3, np.inf])
+    assert np.allclose(oracle.eq1_update(u, c, r, 0.0), [0.1, 0.1, -0.02, 0.2])
+    assert np.allclose(oracle.eq1_update(u, c, r, 0.5), [0.5, 0.2, 0.14, np.inf])
+    s = oracle.signed_output(np.array([0.2, np.inf, 0.1]), np.array([0.3, 0.3, 0.3]),
+                             np.array([3, 0, 2]), np.array([1, 0, 5]))
+    assert np.allclose(s, [0.2, 0.3, -0.1])
+    p = np.array([[0.5, 0.5, 0.5], [0.9, 0.5, 0.5]], np.float32)
+    lo = np.array([[0.6, 0.4, 0.4]], np.float32)
+    hi = np.array([[0.7, 0.6, 0.6]], np.float32)
+    assert list(oracle.reset_rule(p, np.array([0.11, 0.1]), lo, hi)) == [True, False]
+    assert list(oracle.reset_rule(p, np.array([0.09, 0.21]), lo, hi)) == [False, True]

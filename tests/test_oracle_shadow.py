@@ -1,0 +1,145 @@
+"""Pins for the oracle's soft-shadow march and its derivative (Sec. 2.3).
+
+* Trilinear sampling reproduces linear fields exactly and the texel values
+  at texel centres.
+* A ray running parallel to a plane sees a constant h = H, so the penumbra
+  term has the closed form k H (sqrt 3 / 2) / (t - H/2) at every step after
+  the first, and the visibility is its value at the last step inside the
+  volume -- this pins the step rule, the exit rule and the Aaltonen-style
+  penumbra estimate together.
+* Umbra and fully-lit special cases.
+* The reverse-mode derivative agrees with fp64 central finite differences
+  (step 1e-4) of the forward march, kinks excluded.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import scenes as S
+
+BMIN = np.zeros(3)
+
+
+def _linear_grid(n, grad, c0):
+    c = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    return (grad[0] * X + grad[1] * Y + grad[2] * Z + c0).astype(np.float32)
+
+
+def test_trilinear_exact_on_linear_fields():
+    n = 16
+    g = _linear_grid(n, (0.3, -0.7, 0.2), 0.05)
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        q = rng.uniform(0.5 / n, 1 - 0.5 / n, 3)
+        v = oracle.sample(g, n, BMIN, 1.0, q)
+        assert abs(v - (0.3 * q[0] - 0.7 * q[1] + 0.2 * q[2] + 0.05)) < 1e-6
+    # texel centre returns the texel value
+    j = (3, 7, 11)
+    q = (np.array(j) + 0.5) / n
+    assert oracle.sample(g, n, BMIN, 1.0, q) == pytest.approx(float(g[j[2], j[1], j[0]]), abs=1e-12)
+
+
+@pytest.mark.parametrize("H,k,smax_vox,steps", [(0.06, 8.0, 4.0, 64), (0.04, 4.0, 2.0, 64), (0.03, 4.0, 2.0, 64),
+                                                (0.05, 8.0, 1.0, 20), (0.2, 2.0, 8.0, 64)])
+def test_march_parallel_to_plane_closed_form(H, k, smax_vox, steps):
+    n = 32
+    h = 1.0 / n
+    y0 = 0.1
+    grid = _linear_grid(n, (0, 1, 0), -y0)          # SDF = y - y0
+    eps = h
+    smax = smax_vox * h
+    # start point o = p + 2 eps nrm at height H above the plane, x = 0.1
+    p = np.array([[0.1, y0 + H - 2 * eps, 0.5]], np.float32)
+    nrm = np.array([[0, 1, 0]], np.float32)
+    vis = oracle.shadow(grid, n, BMIN, 1.0, p, nrm, (1.0, 0.0, 0.0), k, steps, smax, eps)[0]
+    o = p[0].astype(np.float64) + 2 * eps * nrm[0]
+    Hf = o[1] - y0
+    step = min(Hf, smax)
+    res = 1.0
+    for i in range(steps):
+        t = i * step
+        if o[0] + t > 1.0:
+            break
+        if i >= 1 and t - Hf / 2 > 0:
+            res = min(res, k * Hf * math.sqrt(3) / 2 / (t - Hf / 2))
+    if Hf < eps:
+        res = 0.0                                   # h < eps at the first sample
+    assert vis == pytest.approx(res, rel=2e-6, abs=1e-12)   # grid values are fp32
+
+
+def test_umbra_and_lit():
+    n = 32
+    h = 1.0 / n
+    grid = S.box_grid_sdf(n, (0.5, 0.5, 0.5), 0.25, floor_y=0.1)
+    pos, nrm = S.floor_gbuffer(16, 16, y=0.1, lo=0.4, hi=0.6)
+    vis = oracle.shadow(grid, n, BMIN, 1.0, pos, nrm, (0, 1, 0), 8.0, 64, 4 * h, h)
+    assert np.all(vis == 0.0)                 # straight under the box: umbra
+    pos, nrm = S.floor_gbuffer(16, 16, y=0.1, lo=0.0, hi=0.2)
+    vis = oracle.shadow(grid, n, BMIN, 1.0, pos, nrm, (0, 1, 0), 8.0, 64, 4 * h, h)
+    assert np.all(vis == 1.0)                 # far from the box, light overhead
+
+
+def _fd_setup(n=32, k=2.0):
+    h = 1.0 / n
+    grid = np.minimum(S.sphere_grid_sdf(n, (0.5, 0.35, 0.5), 0.12),
+                      S.box_grid_sdf(n, (0.3, 0.3, 0.65), 0.06)).astype(np.float32)
+    grid = np.minimum(grid, _linear_grid(n, (0, 1, 0), -0.1))       # floor y = 0.1
+    pos, nrm = S.floor_gbuffer(24, 24, y=0.1, lo=0.1, hi=0.9)
+    cfg = dict(k=k, steps=64, step_max=4 * h, eps=h)
+    return n, grid, pos, nrm, cfg
+
+
+def test_gradient_matches_finite_differences():
+    n, grid, pos, nrm, cfg = _fd_setup()
+    Lv = np.array([0.4, 1.0, 0.3])
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=pos.shape[0] * pos.shape[1])
+
+    def loss(g, lv):
+        return float(w @ oracle.shadow(g, n, BMIN, 1.0, pos, nrm, lv, **cfg))
+
+    gs, gl = oracle.shadow_grad(grid, n, BMIN, 1.0, pos, nrm, Lv, dvis=w, **cfg)
+    nz = np.nonzero(gs)[0]
+    assert nz.size > 50
+    pick = np.concatenate([nz[np.argsort(-np.abs(gs[nz]))[:60]], rng.choice(nz, 60, replace=False)])
+    ok = kinks = 0
+    flat = grid.reshape(-1)
+    for j in np.unique(pick):
+        hstep = 1e-4
+        gp = flat.copy(); gp[j] += np.float32(hstep)
+        gm = flat.copy(); gm[j] -= np.float32(hstep)
+        dp = float(gp[j]) - float(flat[j])
+        dm = float(flat[j]) - float(gm[j])
+        l0 = loss(flat, Lv)
+        fp = (loss(gp, Lv) - l0) / dp
+        fm = (l0 - loss(gm, Lv)) / dm
+        if abs(fp - fm) > 0.1 * max(abs(fp), abs(fm), 1e-12):
+            kinks += 1
+            continue
+        fd = (loss(gp, Lv) - loss(gm, Lv)) / (dp + dm)
+        assert abs(fd - gs[j]) <= 1e-3 * max(abs(fd), 1e-3 * np.max(np.abs(gs))), (j, fd, gs[j])
+        ok += 1
+    assert ok >= 60 and kinks <= ok
+    # light direction: FD over the pixels whose march is smooth around L (the
+    # same discrete path -- samples taken, arg-min step, termination -- and
+    # one-sided slopes that agree, so no step-limit or cell-boundary kink)
+    vis0, info0 = oracle.shadow(flat, n, BMIN, 1.0, pos, nrm, Lv, info=True, **cfg)
+    smooth = np.ones(info0.shape[0], bool)
+    central = []
+    for a in range(3):
+        e = np.zeros(3); e[a] = 1e-4
+        vp, ip = oracle.shadow(flat, n, BMIN, 1.0, pos, nrm, Lv + e, info=True, **cfg)
+        vm, im = oracle.shadow(flat, n, BMIN, 1.0, pos, nrm, Lv - e, info=True, **cfg)
+        sp, sm = (vp - vis0) / 1e-4, (vis0 - vm) / 1e-4
+        smooth &= np.all(ip == info0, axis=1) & np.all(im == info0, axis=1)
+        smooth &= np.abs(sp - sm) <= 1e-2 * np.maximum(np.maximum(np.abs(sp), np.abs(sm)), 1e-3)
+        central.append((vp - vm) / 2e-4)
+    assert smooth.mean() > 0.8
+    ws = np.where(smooth, w, 0.0)
+    _, gl = oracle.shadow_grad(grid, n, BMIN, 1.0, pos, nrm, Lv, dvis=ws, **cfg)
+    for a in range(3):
+        fd = float(ws @ central[a])
+        assert abs(fd - gl[a]) <= 1e-3 * max(abs(fd), 1e-6), (a, fd, gl[a])
