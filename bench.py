@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the RTSDF SDF update on one GB300.
+
+Workload (one step = one animated frame of the whole SDF update):
+  coarse 256^3 / fine 512^3 fp32, 500 displaced UV spheres (1,000,000
+  triangles), every object translated by a random vector of length <= 0.5
+  coarse voxel per frame; per frame: move objects, BVH refit, voxelize,
+  jump flood (8 passes), mask + reset in changed regions, trace 64 Philox
+  rays per masked fine texel with the Eq. 1 update.
+
+Metric: SDF update ms/frame (lower is better), with traced rays/s and the
+jump-flood HBM GB/s reported beside it.  Inputs are synthetic (procedural
+scene, seeded), resident in HBM before the timed region; the fine grids
+(3 x 512 MB) exceed the 129 MB L2, so no explicit flush is needed.
+
+--impl reference times the CPU oracle (oracle/) on the host cores on a
+bounded sample of the same frame, extrapolated to ms/frame.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SDF update ms/frame at 256^3->512^3 (animated ~1M tris, 64 rays/texel); traced rays/s; JFA HBM GB/s"
+UNIT = "ms/frame"
+NC, D_VOX, BETA, RAYS, SEED = 256, 2.0, 0.5, 64, 2
+N_OBJ = 500
+
+# fp32 pipe operations per BVH node entered / per ray-triangle test in the
+# tracer's source (fma counted as 2 flops): two slab tests of 6 fma + 15
+# min/max/compare each, one ordering compare; Moller-Trumbore: 3 crosses
+# (3 fma + 3 mul each), 4 dots (2 fma + 1 mul), 3 subtracts, 1 divide
+# (counted as 1), 3 scales, 1 add and 5 compares.
+FLOP_PER_VISIT = 2 * (6 * 2 + 15) + 1
+FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
+
+# DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
+# by the sha256 of the kernel source it was measured on; reported as null
+# once trace.cu changes.
+TRAFFIC = {}
+
+
+def _src_hash(name):
+    p = os.path.join(ROOT, "paper_2210_04449_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rtsdf", choices=["rtsdf", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--objects", type=int, default=N_OBJ, help="sphere count (500 = the 1M-triangle workload)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2210_04449_gb300 import RTSDF
+    from synth import scenes as S
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mesh = S.animated_scene(SEED, n_objects=args.objects)
+    n_frames = args.warmup + args.steps
+    trans = np.stack([S.object_translations(SEED, t, mesh.n_objects, 0.5 / NC) for t in range(n_frames + 1)])
+    trans_dev = torch.tensor(trans, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    rt = RTSDF(NC, beta_vox=BETA, seed=SEED)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.set_objects(mesh.vert_object, mesh.n_objects)
+    rt.build_bvh()
+
+    def frame(t, tr):
+        if t > 0:
+            rt.move_objects(tr)
+            rt.build_bvh(refit=True)
+        rt.voxelize()
+        rt.jfa()
+        rt.trace(D_VOX, RAYS, t)
+
+    frame(0, None)
+    for t in range(1, args.warmup + 1):
+        frame(t, trans_dev[t])
+    rt.sync()
+    rt.set_profiling(True)
+    rt.stats()                          # reset the per-stage sums
+    launches0 = rt.stats()["launches"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(dev.index)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for t in range(args.warmup + 1, args.warmup + 1 + args.steps):
+        frame(t, trans_dev[t])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    st = rt.stats()
+    launches = st["launches"] - launches0
+    rt.sync()
+    n_masked_tex = st["n_masked_texels"]
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_frame = ms_total / args.steps
+    stage = {k: (v / args.steps if st["stage_calls"][k] else None) for k, v in st["stage_ms"].items()}
+
+    # one counted frame (not timed): tracer work per ray
+    rt.set_profiling(False)
+    rt.set_counting(True)
+    tnext = args.warmup + 1 + args.steps
+    frame(tnext, trans_dev[min(tnext, n_frames)])
+    cnt = rt.stats()
+    rt.set_counting(False)
+
+    # end-to-end through the public API with host buffers: per frame the
+    # translations go host (pinned) -> device, and the frame's result
+    # (masked-texel count and device status) comes back to the host
+    trans_host = torch.tensor(trans, dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        t = tnext + 1 + i
+        frame(t, trans_host[(t % n_frames) or 1])
+        rt.masked_count()
+        rt.sync()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+
+    rays_frame = n_masked_tex * RAYS
+    trace_ms = stage["trace"]
+    jfa_ms = stage["jfa"]
+    passes = math.ceil(math.log2(NC))
+    jfa_bytes = passes * NC ** 3 * 8 + NC ** 3 * 4
+    jfa_gbs = jfa_bytes / (jfa_ms * 1e-3) / 1e9 if jfa_ms else None
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+    visits_per_ray = cnt["node_visits"] / max(cnt["rays"], 1)
+    tests_per_ray = cnt["tri_tests"] / max(cnt["rays"], 1)
+    # node entries include the leaves; a leaf entry is one triangle test
+    flop_per_ray = (visits_per_ray - tests_per_ray) * FLOP_PER_VISIT + tests_per_ray * FLOP_PER_TEST
+    trace_tflops = rays_frame * flop_per_ray / (trace_ms * 1e-3) / 1e12 if trace_ms else None
+    th = _src_hash("trace.cu")
+    traffic = TRAFFIC.get(th)
+
+    line = {
+        "metric": METRIC,
+        "value": round(ms_frame / world, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_frame, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded procedural scene: 500 displaced UV spheres, random rigid motion)",
+        "config": {"workload": "animated 256^3->512^3, 500 spheres / 1,000,000 tris, 64 rays/texel, "
+                               "d=2 voxels, beta=0.5, reset in changed regions, per-frame refit+voxelize+JFA",
+                   "coarse_n": NC, "fine_n": 2 * NC, "triangles": int(mesh.nt), "rays_per_texel": RAYS,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (fine grids 3 x 512 MB)"},
+        "gpu_launches": int(launches),
+        "rays_per_s": round(rays_frame / (trace_ms * 1e-3)) if trace_ms else None,
+        "masked_texels": int(n_masked_tex),
+        "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage.items()},
+        "jfa": {"ms": round(jfa_ms, 4) if jfa_ms else None, "passes": passes,
+                "algorithmic_bytes": jfa_bytes, "gbs": round(jfa_gbs, 1) if jfa_gbs else None,
+                "peak_gbs": hbm_peak, "frac": round(jfa_gbs / hbm_peak, 4) if jfa_gbs else None,
+                "peak_source": hbm_src},
+        "tracer": {"node_visits_per_ray": round(visits_per_ray, 2), "tri_tests_per_ray": round(tests_per_ray, 2),
+                   "flop_per_ray": round(flop_per_ray, 1)},
+        "roofline": {"kernel": "k_trace", "bound": "alu",
+                     "achieved": round(trace_tflops, 3) if trace_tflops else None,
+                     "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
+                     "frac": round(trace_tflops / fp32_peak_tflops, 4) if trace_tflops else None,
+                     "traffic": traffic,
+                     "peak_source": f"derived: {sms} SMs x 128 fp32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"},
+        "clocks": clk,
+        "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": N_OBJ * 3 * 4,
+                "d2h_bytes_per_step": 8 + 4},
+    }
+    rt.close()
+    return line, n_masked_tex
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_frame_sample(n_texels, seed=SEED, objects=N_OBJ, masked_texels=None):
+    """Time the oracle (as it stands) on one frame of the same workload:
+    voxelize + jump flood + mask in full, brute-force tracing of n_texels
+    masked texels; returns (extrapolated ms/frame, details)."""
+    import numpy as np
+
+    import oracle
+    from synth import scenes as S
+    mesh = S.animated_scene(seed, n_objects=objects)
+    B = np.zeros(3, np.float32)
+    t0 = time.perf_counter()
+    occ = oracle.voxelize(mesh.verts, mesh.tris, B, 1.0, NC)
+    t1 = time.perf_counter()
+    seeds, _ = oracle.jfa(occ, NC)
+    t2 = time.perf_counter()
+    d2 = oracle.seed_d2(seeds, NC)
+    T = oracle.mask_threshold(D_VOX, BETA)
+    masked = np.nonzero((d2 >= 0) & (d2 <= T))[0]
+    t3 = time.perf_counter()
+    rng = np.random.default_rng(0)
+    pick = rng.choice(masked, size=min(n_texels, masked.size), replace=False)
+    nf = 2 * NC
+    x, y, z = pick % NC, (pick // NC) % NC, pick // (NC * NC)
+    tex = (2 * x) + nf * ((2 * y) + nf * (2 * z))
+    t4 = time.perf_counter()
+    oracle.trace(mesh.verts, mesh.tris, B, 1.0, nf, seed, 1, RAYS, tex)
+    t5 = time.perf_counter()
+    m_tex = masked.size * 8 if masked_texels is None else masked_texels
+    per_texel = (t5 - t4) / max(pick.size, 1)
+    total = (t1 - t0) + (t2 - t1) + (t3 - t2) + per_texel * m_tex
+    return total * 1e3, {"voxelize_s": round(t1 - t0, 3), "jfa_s": round(t2 - t1, 3), "mask_s": round(t3 - t2, 3),
+                         "trace_s_per_texel": round(per_texel, 4), "texels_sampled": int(pick.size),
+                         "masked_texels": int(m_tex), "sample_cpu_s": round(t5 - t0, 2)}
+
+
+def oracle_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    # budget ~2 minutes for the whole run
+    per_step_s = max(8.0, 150.0 / (args.steps + args.warmup))
+    vals, info = [], None
+    for i in range(args.warmup + args.steps):
+        ms, info = oracle_frame_sample(4 if per_step_s < 12 else 8)
+        if i >= args.warmup:
+            vals.append(ms)
+    v = sum(vals) / len(vals)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "animated 256^3->512^3, 500 spheres / 1,000,000 tris, 64 rays/texel"},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                             "sample": f"per step: one frame's voxelize + JFA + mask in full, brute-force trace "
+                                       f"of {info['texels_sampled']} masked texels x {RAYS} rays over all "
+                                       f"triangles, extrapolated to all {info['masked_texels']} masked texels",
+                             "detail": info},
+            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line, m_tex = run_gpu(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            ms, info = oracle_frame_sample(16, masked_texels=m_tex)
+            line["cpu_baseline"] = {
+                "value": round(ms, 1), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                "sample": f"one frame: voxelize + JFA + mask in full, brute-force trace of "
+                          f"{info['texels_sampled']} masked texels x {RAYS} rays over all 1M triangles, "
+                          f"extrapolated to the frame's {info['masked_texels']} masked texels",
+                "detail": info}
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * rtsdf.h -- C ABI of the GB300 (sm_103a) real-time SDF generator.
+ *
+ * Implements the method of "RTSDF: Generating Signed Distance Fields in Real
+ * Time for Soft Shadow Rendering" (Tan, Chua, Koh, Bhojan, Pacific Graphics
+ * 2020): a coarse SDF by voxelization and 3D jump flooding (Sec. 2.1), a
+ * fine SDF by ray tracing fine texels near surfaces with temporal
+ * accumulation (Sec. 2.2, Eq. 1), and soft shadows by sphere tracing the fine
+ * SDF (Sec. 2.3), plus the reverse-mode derivative of the shadow pass.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grids.  The scene bounds are the cube [bmin, bmin + extent]^3.  The coarse
+ *   grid has N = coarse_n voxels per axis (1 <= N <= 256), voxel size
+ *   h_c = extent / N; the fine grid has 2N texels per axis, h_f = h_c / 2.
+ *   Every grid is stored x-fastest: element (x, y, z) at x + n*(y + n*z).
+ *   A voxel/texel value describes its centre, bmin + (i + 0.5) * h.
+ * Streams.  Every call that launches work enqueues it on the context's
+ *   stream (rtsdf_config.stream / rtsdf_set_stream) and returns without
+ *   waiting, except where a call says it synchronises.
+ * Memory.  The library allocates and owns all grids, the mesh copy and the
+ *   BVH (cudaMalloc at creation / upload, cudaFree at destroy).  Caller
+ *   buffers (G-buffers, outputs, gradients) are caller-owned device pointers
+ *   that must stay valid until the enqueued work has finished.
+ * Errors.  Argument and ordering errors are reported synchronously by the
+ *   return value.  Errors found by device code (invalid mesh data found
+ *   after upload, a BVH traversal stack overflow) set a device status word
+ *   that the next rtsdf_sync() returns (and clears).  The library never
+ *   aborts, traps or prints.
+ * Threads.  A context must not be used from two host threads at once;
+ *   distinct contexts are independent.
+ */
+#ifndef RTSDF_H
+#define RTSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtsdf_ctx* rtsdf_t;
+
+typedef enum {
+    RTSDF_OK = 0,
+    RTSDF_E_ARG = 1,       /* invalid argument: null pointer, size or value out of range */
+    RTSDF_E_STATE = 2,     /* call out of order (e.g. rtsdf_jfa before rtsdf_voxelize) */
+    RTSDF_E_OOM = 3,       /* device allocation failed */
+    RTSDF_E_CUDA = 4,      /* CUDA runtime error (launch failure, sticky device error) */
+    RTSDF_E_MESH = 5,      /* triangle index out of range, or a vertex not finite or
+                              outside [bmin - extent/2, bmin + 3 extent/2]^3 */
+    RTSDF_E_OVERFLOW = 6,  /* a BVH traversal exceeded its fixed stack (result incomplete) */
+    RTSDF_E_TIMEOUT = 7    /* a bounded device-side wait expired (batched form) */
+} rtsdf_status;
+
+typedef struct {
+    float bmin[3];      /* lower corner of the scene cube */
+    float extent;       /* edge length of the scene cube, > 0 */
+    int32_t coarse_n;   /* coarse voxels per axis, 1..256; fine grid = 2 * coarse_n */
+    float beta_vox;     /* Sec. 2.1 bias beta, in coarse voxels (>= 0) */
+    float alpha;        /* Eq. 1 decay alpha in [0, 1]; 1 = plain temporal minimum */
+    uint64_t seed;      /* key of the Philox stream for the ray directions */
+    void* stream;       /* cudaStream_t to enqueue on; NULL = legacy default stream */
+} rtsdf_config;
+
+/* Device pointers into the context's grids (borrowed: valid until the next
+ * call that reallocates them, i.e. rtsdf_destroy). */
+typedef struct {
+    int32_t coarse_n, fine_n;
+    const uint32_t* seeds;   /* [coarse_n^3] nearest seed after rtsdf_jfa, packed
+                                x | y << 8 | z << 16; 0xFFFFFFFF = no seed */
+    const float* coarse;     /* [coarse_n^3] coarse SDF c = h_c (sqrt(D2) - beta); +inf = no seed */
+    const float* fine;       /* [fine_n^3] signed fine SDF f_t (Eq. 1 and the sign vote) */
+    const float* accum;      /* [fine_n^3] unsigned accumulator u_t of traced texels; +inf = none */
+    const uint32_t* counts;  /* [fine_n^3] front-hit count | back-hit count << 16 (saturating) */
+    const uint32_t* masked;  /* [n_masked_coarse] coarse voxels whose 8 fine texels were traced */
+} rtsdf_grids;
+
+/* Pipeline stages, in the order of rtsdf_stats.stage_ms / stage_calls. */
+typedef enum {
+    RTSDF_STAGE_VOXELIZE = 0, RTSDF_STAGE_JFA = 1, RTSDF_STAGE_MASK = 2, RTSDF_STAGE_TRACE = 3,
+    RTSDF_STAGE_BVH = 4, RTSDF_STAGE_SHADOW = 5, RTSDF_STAGE_SHADOW_BWD = 6, RTSDF_STAGE_MOTION = 7,
+    RTSDF_STAGE_COUNT = 8
+} rtsdf_stage;
+
+typedef struct {
+    int64_t launches;         /* kernels launched by this context since creation */
+    int64_t n_masked_texels;  /* fine texels traced by the last rtsdf_trace (8 per masked voxel) */
+    int32_t jfa_passes;       /* passes run by the last rtsdf_jfa */
+    int32_t bvh_depth;        /* depth of the BVH (0 before the first build) */
+    /* Device time (CUDA events on the context stream) summed over the calls
+       of each stage since the previous rtsdf_get_stats, and the number of
+       those calls; only while profiling is on (rtsdf_set_profiling). */
+    float stage_ms[RTSDF_STAGE_COUNT];
+    int32_t stage_calls[RTSDF_STAGE_COUNT];
+    /* Tracer work since the previous rtsdf_get_stats, only while counting is
+       on (rtsdf_set_counting): rays cast, BVH nodes entered, ray/triangle
+       tests. */
+    int64_t rays, node_visits, tri_tests;
+} rtsdf_stats;
+
+/* Sec. 2: create a context (allocates both grids on the current device).
+ * Returns RTSDF_E_ARG for an invalid config, RTSDF_E_OOM when the grids do
+ * not fit. */
+rtsdf_status rtsdf_create(const rtsdf_config* cfg, rtsdf_t* out);
+
+/* Frees every device buffer of the context (synchronises its stream first). */
+rtsdf_status rtsdf_destroy(rtsdf_t ctx);
+
+/* Changes the stream later calls enqueue on. */
+rtsdf_status rtsdf_set_stream(rtsdf_t ctx, void* stream);
+
+/* Sec. 2.1 input: copy a triangle mesh into the context.  verts: float32
+ * [nv, 3]; tris: int32 [nt, 3] (counter-clockwise seen from outside = front
+ * face).  on_device != 0: both pointers are device pointers, else host.
+ * Validates the data (synchronises) and returns RTSDF_E_MESH for an index
+ * outside [0, nv) or a vertex that is not finite or lies outside
+ * [bmin - extent/2, bmin + 3 extent/2]^3.  nt = 0 is an empty scene.
+ * Resets the accumulated fine SDF and invalidates the BVH. */
+rtsdf_status rtsdf_upload_mesh(rtsdf_t ctx, const float* verts, int64_t nv,
+                               const int32_t* tris, int64_t nt, int on_device);
+
+/* Rigid objects for animated scenes: vert_object int32 [nv] gives each
+ * vertex's object id in [0, n_objects).  Host or device pointer. */
+rtsdf_status rtsdf_set_objects(rtsdf_t ctx, const int32_t* vert_object, int32_t n_objects,
+                               int on_device);
+
+/* Moves every object by its translation (float32 [n_objects, 3], host or
+ * device pointer): v += t[object(v)] in fp32.  Records the previous
+ * bounding box of every object with a non-zero translation; the next
+ * rtsdf_trace restarts the accumulation of traced texels whose centre lies
+ * within their accumulated distance of such a box (reset in changed
+ * regions).  Vertices that leave the accepted box set RTSDF_E_MESH at the
+ * next rtsdf_sync and are clamped. */
+rtsdf_status rtsdf_move_objects(rtsdf_t ctx, const float* translations, int on_device);
+
+/* Builds (refit = 0) a linear BVH over the uploaded triangles (30-bit Morton
+ * order, one triangle per leaf), or recomputes its boxes for the current
+ * vertex positions keeping the topology (refit = 1; requires a build). */
+rtsdf_status rtsdf_build_bvh(rtsdf_t ctx, int refit);
+
+/* Sec. 2.1: conservative voxelization.  A coarse voxel is a seed iff some
+ * closed triangle meets the closed voxel cube (vertices quantised to 1/256
+ * voxel, exact integer separating-axis test). */
+rtsdf_status rtsdf_voxelize(rtsdf_t ctx);
+
+/* Sec. 2.1: 3D jump flooding with steps 2^(ceil(log2 N) - 1), ..., 1; each
+ * pass takes, per voxel, the nearest seed among the 27 voxels v + {-k,0,k}^3
+ * of the previous pass (ties: smaller linear seed index), and the last pass
+ * writes the coarse SDF c = h_c sqrt(D2) - beta h_c (fp32). */
+rtsdf_status rtsdf_jfa(rtsdf_t ctx);
+
+/* Sec. 2.2 / Eq. 1 for frame `frame`: fine texels whose parent coarse voxel
+ * has c <= d_vox * h_c are traced with rays_per_texel (a power of two,
+ * 1..1024) random directions from Philox-4x32-10 keyed by (texel, frame,
+ * ray); the smallest closest-hit distance r_t updates the accumulator
+ * u_t = min(alpha u_{t-1} + (1 - alpha) c_t, r_t) and the front/back hit
+ * counts; f_t = +-u_t (minus when back hits outnumber front hits), or c_t
+ * while no ray has hit.  Texels with c > d_vox * h_c get f_t = c_t and
+ * restart their accumulation.  Requires rtsdf_jfa and rtsdf_build_bvh. */
+rtsdf_status rtsdf_trace(rtsdf_t ctx, float d_vox, int32_t rays_per_texel, int32_t frame);
+
+/* Sec. 2.3: soft-shadow visibility.  sdf: float32 [(2N)^3] device grid
+ * (NULL = the context's fine SDF).  pos, nrm: float32 [npix, 3] device
+ * shading points and unit normals.  light: direction towards the light
+ * (host, normalised internally).  Per point the march starts at
+ * pos + 2 eps nrm, samples the trilinear SDF, stops with visibility 0 when
+ * h < eps, and otherwise returns clamp(min_i k dd_i / (t_i - y_i), 0, 1) over
+ * at most `steps` samples (the Aaltonen penumbra estimate), stepping
+ * min(h, step_max).  eps = eps_vox h_f, step_max = step_max_vox h_f.
+ * vis: float32 [npix] device output.  steps in [1, 256]. */
+rtsdf_status rtsdf_shadow(rtsdf_t ctx, const float* sdf, const float* pos, const float* nrm,
+                          int64_t npix, const float light[3], float k, int32_t steps,
+                          float step_max_vox, float eps_vox, float* vis);
+
+/* Reverse-mode derivative of rtsdf_shadow (the march is recomputed, not
+ * stored).  dvis: float32 [npix] dLoss/dvis.  Accumulates (+=) dLoss/dsdf
+ * into dsdf (float32 [(2N)^3], caller-zeroed) and dLoss/dlight into
+ * dlight (float32 [3] device, w.r.t. the unnormalised light vector). */
+rtsdf_status rtsdf_shadow_backward(rtsdf_t ctx, const float* sdf, const float* pos,
+                                   const float* nrm, int64_t npix, const float light[3], float k,
+                                   int32_t steps, float step_max_vox, float eps_vox,
+                                   const float* dvis, float* dsdf, float* dlight);
+
+/* Borrowed device views of the grids (no synchronisation). */
+rtsdf_status rtsdf_get_grids(rtsdf_t ctx, rtsdf_grids* out);
+
+/* Number of masked coarse voxels of the last rtsdf_trace (synchronises). */
+rtsdf_status rtsdf_get_masked_count(rtsdf_t ctx, int64_t* n_masked_coarse);
+
+/* Statistics (synchronises; resets the per-stage sums and the counters). */
+rtsdf_status rtsdf_get_stats(rtsdf_t ctx, rtsdf_stats* out);
+
+/* Per-stage event timing on / off (off by default). */
+rtsdf_status rtsdf_set_profiling(rtsdf_t ctx, int on);
+
+/* Tracer work counters on / off (off by default; adds atomics to the tracer,
+   so timed runs leave it off). */
+rtsdf_status rtsdf_set_counting(rtsdf_t ctx, int on);
+
+/* Checkpoint of the temporal state (accumulator, counts, fine SDF): bytes
+ * needed / copy to a host buffer (synchronises) / restore.  Because ray
+ * directions depend only on (seed, texel, frame, ray), a restored context
+ * continues bit-identically. */
+rtsdf_status rtsdf_state_size(rtsdf_t ctx, size_t* bytes);
+rtsdf_status rtsdf_save_state(rtsdf_t ctx, void* host_buf, size_t bytes);
+rtsdf_status rtsdf_load_state(rtsdf_t ctx, const void* host_buf, size_t bytes);
+
+/* Waits for the context's stream and returns (then clears) any error
+ * recorded by device code; RTSDF_E_CUDA on a CUDA error. */
+rtsdf_status rtsdf_sync(rtsdf_t ctx);
+
+/* Static description of a status code. */
+const char* rtsdf_status_str(rtsdf_status s);
+
+/* Library version, "major.minor.patch". */
+const char* rtsdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTSDF_H */

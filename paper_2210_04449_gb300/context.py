@@ -1,0 +1,223 @@
+"""Python binding of the RTSDF C ABI (argument marshalling only).
+
+Every step of the pipeline runs in librtsdf's CUDA kernels; PyTorch provides
+device memory for caller-owned buffers and the CUDA stream.  Method names
+follow the C entry points of ``include/rtsdf.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import call
+
+
+class _CudaView:
+    """Zero-copy descriptor of a device buffer (``__cuda_array_interface__``)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _host_or_device(a, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            t = a.detach().contiguous()
+            want = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+            if t.dtype != want:
+                t = t.to(want)
+            return t.data_ptr(), int(t.is_cuda), t
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, 0, arr
+
+
+class RTSDF:
+    """One SDF generator context (coarse grid N^3, fine grid (2N)^3) on one GPU.
+
+    Sec. 2 of the paper: voxelize -> jump flood (coarse SDF, Sec. 2.1) ->
+    mask + ray trace with Eq. 1 accumulation (fine SDF, Sec. 2.2) -> soft
+    shadows (Sec. 2.3).
+    """
+
+    def __init__(self, coarse_n: int, bmin=(0.0, 0.0, 0.0), extent: float = 1.0, beta_vox: float = 0.5,
+                 alpha: float = 1.0, seed: int = 0, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("RTSDF needs a CUDA device (sm_103a); there is no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            cfg = _abi.Config()
+            cfg.bmin = (ctypes.c_float * 3)(*[float(b) for b in bmin])
+            cfg.extent = float(extent)
+            cfg.coarse_n = int(coarse_n)
+            cfg.beta_vox = float(beta_vox)
+            cfg.alpha = float(alpha)
+            cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+            cfg.stream = self.stream.cuda_stream
+            h = ctypes.c_void_p()
+            call("rtsdf_create", ctypes.byref(cfg), ctypes.byref(h))
+        self._h = h
+        self.coarse_n = int(coarse_n)
+        self.fine_n = 2 * int(coarse_n)
+        self.bmin = tuple(float(b) for b in bmin)
+        self.extent = float(extent)
+        self.beta_vox, self.alpha, self.seed = float(beta_vox), float(alpha), int(seed)
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _abi.lib().rtsdf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def set_stream(self, stream) -> None:
+        call("rtsdf_set_stream", self._h, stream.cuda_stream)
+        self.stream = stream
+
+    # ------------------------------------------------------------ scene
+    def upload_mesh(self, verts, tris) -> None:
+        pv, dv, kv = _host_or_device(verts, np.float32)
+        pt, dt, kt = _host_or_device(tris, np.int32)
+        if dv != dt:
+            raise ValueError("verts and tris must both be host or both be device buffers")
+        nv = int(np.prod(kv.shape)) // 3
+        nt = int(np.prod(kt.shape)) // 3
+        call("rtsdf_upload_mesh", self._h, pv, nv, pt, nt, dv)
+
+    def set_objects(self, vert_object, n_objects: int) -> None:
+        p, d, k = _host_or_device(vert_object, np.int32)
+        call("rtsdf_set_objects", self._h, p, int(n_objects), d)
+
+    def move_objects(self, translations) -> None:
+        p, d, k = _host_or_device(translations, np.float32)
+        call("rtsdf_move_objects", self._h, p, d)
+        self._keep = k   # device buffers must outlive the enqueued copy
+
+    def build_bvh(self, refit: bool = False) -> None:
+        call("rtsdf_build_bvh", self._h, int(bool(refit)))
+
+    # ------------------------------------------------------------ Sec. 2.1-2.2
+    def voxelize(self) -> None:
+        call("rtsdf_voxelize", self._h)
+
+    def jfa(self) -> None:
+        call("rtsdf_jfa", self._h)
+
+    def trace(self, d_vox: float, rays_per_texel: int, frame: int) -> None:
+        call("rtsdf_trace", self._h, float(d_vox), int(rays_per_texel), int(frame))
+
+    def update(self, d_vox: float, rays_per_texel: int, frame: int) -> None:
+        """One frame of Sec. 2.1-2.2: voxelize, jump flood, mask and trace."""
+        self.voxelize()
+        self.jfa()
+        self.trace(d_vox, rays_per_texel, frame)
+
+    # ------------------------------------------------------------ Sec. 2.3
+    @staticmethod
+    def _light3(light):
+        import torch
+        if isinstance(light, torch.Tensor):
+            light = light.detach().double().cpu().numpy()
+        l = [float(x) for x in np.asarray(light, dtype=np.float64).reshape(3)]
+        return (ctypes.c_float * 3)(*l)
+
+    def shadow(self, pos, nrm, light, k: float = 8.0, steps: int = 64, step_max_vox: float = 4.0,
+               eps_vox: float = 1.0, sdf=None, out=None):
+        import torch
+        pos = pos.contiguous()
+        nrm = nrm.contiguous()
+        npix = pos.numel() // 3
+        vis = out if out is not None else torch.empty(pos.shape[:-1], device=pos.device, dtype=torch.float32)
+        sp = 0 if sdf is None else sdf.contiguous().data_ptr()
+        call("rtsdf_shadow", self._h, sp, pos.data_ptr(), nrm.data_ptr(), npix, self._light3(light), float(k),
+             int(steps), float(step_max_vox), float(eps_vox), vis.data_ptr())
+        return vis
+
+    def shadow_backward(self, pos, nrm, light, dvis, dsdf, dlight, k: float = 8.0, steps: int = 64,
+                        step_max_vox: float = 4.0, eps_vox: float = 1.0, sdf=None) -> None:
+        pos = pos.contiguous()
+        nrm = nrm.contiguous()
+        dvis = dvis.contiguous()
+        sp = 0 if sdf is None else sdf.contiguous().data_ptr()
+        call("rtsdf_shadow_backward", self._h, sp, pos.data_ptr(), nrm.data_ptr(), pos.numel() // 3,
+             self._light3(light), float(k), int(steps), float(step_max_vox), float(eps_vox), dvis.data_ptr(),
+             dsdf.data_ptr(), dlight.data_ptr())
+
+    # ------------------------------------------------------------ inspection
+    def grids(self) -> dict:
+        """Zero-copy torch views of the context's grids (valid while it lives)."""
+        import torch
+        g = _abi.Grids()
+        call("rtsdf_get_grids", self._h, ctypes.byref(g))
+        nc3, nf3 = self.coarse_n ** 3, self.fine_n ** 3
+        dev = self.device
+
+        def view(ptr, n, ts):
+            return torch.as_tensor(_CudaView(ptr, (n,), ts), device=dev)
+
+        return {
+            "seeds": view(g.seeds, nc3, "<u4"),
+            "coarse": view(g.coarse, nc3, "<f4"),
+            "fine": view(g.fine, nf3, "<f4"),
+            "accum": view(g.accum, nf3, "<f4"),
+            "counts": view(g.counts, nf3, "<u4"),
+            "masked": view(g.masked, max(self.masked_count(), 1), "<u4"),
+        }
+
+    def masked_count(self) -> int:
+        n = ctypes.c_int64()
+        call("rtsdf_get_masked_count", self._h, ctypes.byref(n))
+        return int(n.value)
+
+    def set_profiling(self, on: bool) -> None:
+        call("rtsdf_set_profiling", self._h, int(bool(on)))
+
+    def set_counting(self, on: bool) -> None:
+        call("rtsdf_set_counting", self._h, int(bool(on)))
+
+    def stats(self) -> dict:
+        """Counters and per-stage device ms since the previous call."""
+        s = _abi.Stats()
+        call("rtsdf_get_stats", self._h, ctypes.byref(s))
+        out = {name: getattr(s, name) for name in ("launches", "n_masked_texels", "jfa_passes", "bvh_depth",
+                                                    "rays", "node_visits", "tri_tests")}
+        out["stage_ms"] = {k: float(s.stage_ms[i]) for i, k in enumerate(_abi.STAGES)}
+        out["stage_calls"] = {k: int(s.stage_calls[i]) for i, k in enumerate(_abi.STAGES)}
+        return out
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        call("rtsdf_state_size", self._h, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        call("rtsdf_save_state", self._h, ctypes.addressof(buf), n.value)
+        return buf.raw
+
+    def load_state(self, data: bytes) -> None:
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        call("rtsdf_load_state", self._h, ctypes.addressof(buf), len(data))
+
+    def sync(self) -> None:
+        call("rtsdf_sync", self._h)

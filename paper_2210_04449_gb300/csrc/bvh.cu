@@ -1,0 +1,385 @@
+// Acceleration structure for the Sec. 2.2 closest-hit ray casts.
+//
+// The paper does not describe its ray-tracing structure.  This is a linear
+// BVH: triangles ordered by the 30-bit Morton code of their centroid
+// (stable LSD radix sort, so equal codes keep triangle order), the binary
+// hierarchy of Karras ("Maximizing parallelism in the construction of BVHs,
+// octrees and k-d trees", HPG 2012) over the unique keys (code, index), and
+// child boxes filled bottom-up with one atomic counter per node.  A refit
+// recomputes the leaf data and boxes for moved vertices with the same
+// topology.  Leaf boxes are padded outward by 2^-16 extent (+ 2^-18 of the
+// coordinate) so that fp32 rounding in the box test can never cull a
+// triangle that the fp32 ray/triangle test would hit.
+//
+// Also here: the rigid per-object motion of animated scenes.
+#include <math_constants.h>
+
+#include "internal.cuh"
+
+namespace rtsdf {
+
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
+                         float lx, float ly, float lz, float inv_w, uint32_t* __restrict__ keys,
+                         int32_t* __restrict__ vals) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    float c[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; k++) {
+        const float* p = verts + 3 * (int64_t)tris[3 * t + k];
+        c[0] += p[0];
+        c[1] += p[1];
+        c[2] += p[2];
+    }
+    const float l[3] = {lx, ly, lz};
+    uint32_t cell[3];
+    for (int a = 0; a < 3; a++) {
+        float u = (c[a] * (1.f / 3.f) - l[a]) * inv_w * 1024.f;
+        u = fminf(fmaxf(u, 0.f), 1023.f);
+        cell[a] = (uint32_t)u;
+    }
+    keys[t] = spread10(cell[0]) | (spread10(cell[1]) << 1) | (spread10(cell[2]) << 2);
+    vals[t] = (int32_t)t;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                      uint32_t* __restrict__ hist, int nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        int64_t e = base + it * SORT_THREADS + threadIdx.x;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of `total` counters, one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan(uint32_t* __restrict__ a, int64_t total) {
+    __shared__ uint32_t part[1024];
+    const int64_t per = (total + 1023) / 1024;
+    const int64_t lo = threadIdx.x * per, hi = min(lo + per, total);
+    uint32_t s = 0;
+    for (int64_t i = lo; i < hi; i++) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int64_t i = lo; i < hi; i++) {
+        uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+// stable scatter: element order inside a block is (item, warp, lane)
+__global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t* __restrict__ kin,
+                                                         const int32_t* __restrict__ vin,
+                                                         uint32_t* __restrict__ kout, int32_t* __restrict__ vout,
+                                                         int64_t n, int shift, const uint32_t* __restrict__ hist,
+                                                         int nblocks) {
+    __shared__ uint32_t base[257];
+    base[threadIdx.x] = hist[(size_t)threadIdx.x * nblocks + blockIdx.x];
+    if (threadIdx.x == 0) base[256] = 0;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t b0 = (int64_t)blockIdx.x * SORT_TILE;
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        const int64_t e = b0 + it * SORT_THREADS + threadIdx.x;
+        const bool valid = e < n;
+        uint32_t k = 0;
+        int32_t v = 0;
+        uint32_t d = 256;
+        if (valid) {
+            k = kin[e];
+            v = vin[e];
+            d = (k >> shift) & 0xFF;
+        }
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t rank = __popc(peers & lt);
+        const bool leader = (peers & lt) == 0;
+        uint32_t pos = 0;
+        for (unsigned w = 0; w < SORT_THREADS / 32; w++) {
+            if (warp == w) {
+                pos = base[d] + rank;
+                __syncwarp();
+                if (leader) base[d] += __popc(peers);
+            }
+            __syncthreads();
+        }
+        if (valid) {
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ mk, const int32_t* __restrict__ mv, int64_t n,
+                                     int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    const unsigned long long a = ((unsigned long long)mk[i] << 32) | (uint32_t)mv[i];
+    const unsigned long long b = ((unsigned long long)mk[j] << 32) | (uint32_t)mv[j];
+    return __clzll(a ^ b);
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ mk, const int32_t* __restrict__ mv, int64_t n,
+                         BNode* __restrict__ nodes, int32_t* __restrict__ leaf_parent) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (delta(mk, mv, n, i, i + 1) - delta(mk, mv, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(mk, mv, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(mk, mv, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+        if (delta(mk, mv, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(mk, mv, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(mk, mv, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int64_t g = i + s * d + min(d, 0);
+    const int64_t lo = min(i, j), hi = max(i, j);
+    int left, right;
+    if (lo == g) { left = ~(int)g; leaf_parent[g] = (int)i; }
+    else { left = (int)g; nodes[g].d.z = (int)i; }
+    if (hi == g + 1) { right = ~(int)(g + 1); leaf_parent[g + 1] = (int)i; }
+    else { right = (int)(g + 1); nodes[g + 1].d.z = (int)i; }
+    nodes[i].d.x = left;
+    nodes[i].d.y = right;
+    if (i == 0) nodes[0].d.z = -1;
+}
+
+__device__ __forceinline__ float pad_lo(float v, float pad) { return v - (pad + fabsf(v) * 0x1p-18f); }
+__device__ __forceinline__ float pad_hi(float v, float pad) { return v + (pad + fabsf(v) * 0x1p-18f); }
+
+__device__ __forceinline__ void store_child(BNode* node, bool right, const float lo[3], const float hi[3]) {
+    float* a = right ? &node->b.x : &node->a.x;
+    a[0] = lo[0]; a[1] = hi[0]; a[2] = lo[1]; a[3] = hi[1];
+    float* c = &node->c.x + (right ? 2 : 0);
+    c[0] = lo[2]; c[1] = hi[2];
+}
+
+// Leaf data + bottom-up boxes.  One thread per leaf.
+__global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                            const int32_t* order, int64_t n, float4* __restrict__ tri, int32_t* leaf_tri, const int32_t* __restrict__ leaf_parent,
+                            BNode* nodes, uint32_t* flags, float pad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t t = order[i];
+    const float* p0 = verts + 3 * (int64_t)tris[3 * (int64_t)t];
+    const float* p1 = verts + 3 * (int64_t)tris[3 * (int64_t)t + 1];
+    const float* p2 = verts + 3 * (int64_t)tris[3 * (int64_t)t + 2];
+    const float v0[3] = {p0[0], p0[1], p0[2]}, v1[3] = {p1[0], p1[1], p1[2]}, v2[3] = {p2[0], p2[1], p2[2]};
+    tri[3 * i + 0] = make_float4(v0[0], v0[1], v0[2], __int_as_float(t));
+    tri[3 * i + 1] = make_float4(__fsub_rn(v1[0], v0[0]), __fsub_rn(v1[1], v0[1]), __fsub_rn(v1[2], v0[2]), 0.f);
+    tri[3 * i + 2] = make_float4(__fsub_rn(v2[0], v0[0]), __fsub_rn(v2[1], v0[1]), __fsub_rn(v2[2], v0[2]), 0.f);
+    leaf_tri[i] = t;
+    if (n == 1) return;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = pad_lo(fminf(v0[a], fminf(v1[a], v2[a])), pad);
+        hi[a] = pad_hi(fmaxf(v0[a], fmaxf(v1[a], v2[a])), pad);
+    }
+    int child = ~(int)i;
+    int node = leaf_parent[i];
+    // a tree over n leaves has depth < n; the guard only bounds the loop
+    for (int64_t guard = 0; node >= 0 && guard < n; guard++) {
+        BNode* nd = nodes + node;
+        const bool right = nd->d.y == child;
+        store_child(nd, right, lo, hi);
+        __threadfence();
+        if (atomicAdd(flags + node, 1u) != 1u) return;   // first arrival: the sibling finishes this node
+        __threadfence();
+        // both children present: box of this node = union of its two child boxes
+        const volatile float* a = &nd->a.x;
+        const volatile float* b = &nd->b.x;
+        const volatile float* c = &nd->c.x;
+        lo[0] = fminf(a[0], b[0]); hi[0] = fmaxf(a[1], b[1]);
+        lo[1] = fminf(a[2], b[2]); hi[1] = fmaxf(a[3], b[3]);
+        lo[2] = fminf(c[0], c[2]); hi[2] = fmaxf(c[1], c[3]);
+        child = node;
+        node = nd->d.z;
+    }
+}
+
+__global__ void k_depth(const int32_t* __restrict__ leaf_parent, const BNode* __restrict__ nodes, int64_t n,
+                        int32_t* depth) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int d = 1;
+    int node = n > 1 ? leaf_parent[i] : -1;
+    while (node >= 0 && d < 4096) {
+        d++;
+        node = nodes[node].d.z;
+    }
+    atomicMax(depth, d);
+}
+
+// ---------------------------------------------------------------- motion
+__global__ void k_obj_boxes_init(float* boxes, int n_obj) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_obj) return;
+    for (int a = 0; a < 3; a++) {
+        boxes[6 * i + a] = CUDART_INF_F;
+        boxes[6 * i + 3 + a] = -CUDART_INF_F;
+    }
+}
+
+__device__ __forceinline__ void atomic_min_f(float* a, float v) {
+    if (v >= 0.f) atomicMin(reinterpret_cast<int*>(a), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float* a, float v) {
+    if (v >= 0.f) atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));
+    else atomicMin(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
+}
+
+// Box of every moved object (before the move), then v += t[obj].
+__global__ void k_obj_boxes(const float* __restrict__ verts, const int32_t* __restrict__ vobj, int64_t nv,
+                            const float* __restrict__ trans, float* boxes) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    const int o = vobj[i];
+    const float* t = trans + 3 * o;
+    if (t[0] == 0.f && t[1] == 0.f && t[2] == 0.f) return;
+    for (int a = 0; a < 3; a++) {
+        atomic_min_f(boxes + 6 * o + a, verts[3 * i + a]);
+        atomic_max_f(boxes + 6 * o + 3 + a, verts[3 * i + a]);
+    }
+}
+
+__global__ void k_moved_list(const float* __restrict__ trans, int n_obj, int32_t* list, int32_t* count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_obj) return;
+    const float* t = trans + 3 * i;
+    if (t[0] != 0.f || t[1] != 0.f || t[2] != 0.f) list[atomicAdd(count, 1)] = i;
+}
+
+__global__ void k_translate(float* __restrict__ verts, const int32_t* __restrict__ vobj, int64_t nv,
+                            const float* __restrict__ trans) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv * 3) return;
+    const int64_t v = i / 3;
+    const int a = (int)(i % 3);
+    verts[i] = __fadd_rn(verts[i], trans[3 * vobj[v] + a]);
+}
+
+}  // namespace
+
+cudaError_t launch_bvh_build(rtsdf_ctx* c) {
+    Bvh& b = c->bvh;
+    const int64_t n = c->nt;
+    b.nt = n;
+    b.built = false;
+    if (n == 0) {
+        b.depth = 0;
+        b.built = true;
+        return cudaSuccess;
+    }
+    cudaError_t e;
+    // buffers (synchronous allocation: builds are not on the per-frame path)
+    auto realloc_if = [&](void** p, size_t bytes) -> cudaError_t {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+        return cudaMalloc(p, bytes > 0 ? bytes : 16);
+    };
+    const int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    if ((e = realloc_if((void**)&b.nodes, sizeof(BNode) * (size_t)(n > 1 ? n - 1 : 1)))) return e;
+    if ((e = realloc_if((void**)&b.tri, sizeof(float4) * 3 * (size_t)n))) return e;
+    if ((e = realloc_if((void**)&b.leaf_tri, sizeof(int32_t) * (size_t)n))) return e;
+    if ((e = realloc_if((void**)&b.leaf_parent, sizeof(int32_t) * (size_t)n))) return e;
+    if ((e = realloc_if((void**)&b.flags, sizeof(uint32_t) * (size_t)n))) return e;
+    uint32_t *k0 = nullptr, *k1 = nullptr, *hist = nullptr;
+    int32_t *v0 = nullptr, *v1 = nullptr, *depth = nullptr;
+    if ((e = cudaMalloc(&k0, sizeof(uint32_t) * n)) || (e = cudaMalloc(&k1, sizeof(uint32_t) * n)) ||
+        (e = cudaMalloc(&v0, sizeof(int32_t) * n)) || (e = cudaMalloc(&v1, sizeof(int32_t) * n)) ||
+        (e = cudaMalloc(&hist, sizeof(uint32_t) * 256 * (size_t)nblocks)) || (e = cudaMalloc(&depth, sizeof(int32_t)))) {
+        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(depth);
+        return e;
+    }
+    const float w = 2.f * c->cfg.extent;
+    const float lx = c->cfg.bmin[0] - 0.5f * c->cfg.extent, ly = c->cfg.bmin[1] - 0.5f * c->cfg.extent,
+                lz = c->cfg.bmin[2] - 0.5f * c->cfg.extent;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    RTSDF_LAUNCH(c, k_morton, g, 256, 0, c->verts, c->tris, n, lx, ly, lz, 1.f / w, k0, v0);
+    uint32_t* kin = k0; uint32_t* kout = k1;
+    int32_t* vin = v0; int32_t* vout = v1;
+    for (int shift = 0; shift < 32; shift += 8) {
+        RTSDF_LAUNCH(c, k_hist, nblocks, SORT_THREADS, 0, kin, n, shift, hist, nblocks);
+        RTSDF_LAUNCH(c, k_scan, 1, 1024, 0, hist, (int64_t)256 * nblocks);
+        RTSDF_LAUNCH(c, k_scatter, nblocks, SORT_THREADS, 0, kin, vin, kout, vout, n, shift, hist, nblocks);
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        int32_t* tv = vin; vin = vout; vout = tv;
+    }
+    // sorted keys in kin, triangle order in vin
+    if (n > 1) RTSDF_LAUNCH(c, k_karras, (unsigned)((n - 1 + 255) / 256), 256, 0, kin, vin, n, b.nodes, b.leaf_parent);
+    cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, c->stream);
+    const float pad = c->cfg.extent * 0x1p-16f;
+    RTSDF_LAUNCH(c, k_leaves_up, g, 256, 0, c->verts, c->tris, vin, n, b.tri, b.leaf_tri, b.leaf_parent, b.nodes,
+                 b.flags, pad);
+    cudaMemsetAsync(depth, 0, sizeof(int32_t), c->stream);
+    RTSDF_LAUNCH(c, k_depth, g, 256, 0, b.leaf_parent, b.nodes, n, depth);
+    e = cudaGetLastError();
+    int32_t hd = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hd, depth, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(depth);
+    if (e != cudaSuccess) return e;
+    b.depth = hd;
+    b.built = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_bvh_refit(rtsdf_ctx* c) {
+    Bvh& b = c->bvh;
+    const int64_t n = b.nt;
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, c->stream);
+    if (e != cudaSuccess) return e;
+    const float pad = c->cfg.extent * 0x1p-16f;
+    RTSDF_LAUNCH(c, k_leaves_up, (unsigned)((n + 255) / 256), 256, 0, c->verts, c->tris, b.leaf_tri, n, b.tri,
+                 b.leaf_tri, b.leaf_parent, b.nodes, b.flags, pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_move(rtsdf_ctx* c) {
+    const int n_obj = c->n_obj;
+    cudaError_t e = cudaMemsetAsync(c->d_moved_count, 0, sizeof(int32_t), c->stream);
+    if (e != cudaSuccess) return e;
+    RTSDF_LAUNCH(c, k_obj_boxes_init, (n_obj + 127) / 128, 128, 0, c->obj_box, n_obj);
+    RTSDF_LAUNCH(c, k_moved_list, (n_obj + 127) / 128, 128, 0, c->obj_trans, n_obj, c->moved_list, c->d_moved_count);
+    if (c->nv > 0) {
+        RTSDF_LAUNCH(c, k_obj_boxes, (unsigned)((c->nv + 255) / 256), 256, 0, c->verts, c->vert_obj, c->nv,
+                     c->obj_trans, c->obj_box);
+        RTSDF_LAUNCH(c, k_translate, (unsigned)((c->nv * 3 + 255) / 256), 256, 0, c->verts, c->vert_obj, c->nv,
+                     c->obj_trans);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rtsdf

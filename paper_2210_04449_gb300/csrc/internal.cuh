@@ -1,0 +1,155 @@
+// Internal declarations shared by the CUDA translation units of librtsdf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rtsdf.h"
+
+namespace rtsdf {
+
+// Device status bits (accumulated with atomicOr, read by rtsdf_sync).
+enum : uint32_t {
+    ERR_MESH = 1u,
+    ERR_STACK = 2u,
+    ERR_TIMEOUT = 4u,
+};
+
+// Packed seed coordinate: x | y << 8 | z << 16 (N <= 256), EMPTY = all ones.
+// Packed order equals linear-index order, so "smaller packed" is the
+// smaller-linear-index tie-break of the jump flood.
+constexpr uint32_t SEED_EMPTY = 0xFFFFFFFFu;
+constexpr int QSUB = 256;          // vertex quantisation steps per coarse voxel
+constexpr int MAX_N = 256;         // coarse voxels per axis
+constexpr int TRACE_STACK = 64;    // BVH traversal stack depth per ray
+constexpr int MAX_SHADOW_STEPS = 256;
+
+__host__ __device__ inline uint32_t pack_seed(uint32_t x, uint32_t y, uint32_t z) {
+    return x | (y << 8) | (z << 16);
+}
+
+// Binary BVH node: the two child boxes side by side (one 64-byte fetch
+// decides both children).  Child index >= 0: internal node; < 0: ~leaf,
+// where a leaf is a triangle position in Morton order.
+struct __align__(16) BNode {
+    float4 a;   // lo_l.x, hi_l.x, lo_l.y, hi_l.y
+    float4 b;   // lo_r.x, hi_r.x, lo_r.y, hi_r.y
+    float4 c;   // lo_l.z, hi_l.z, lo_r.z, hi_r.z
+    int4 d;     // left, right, parent, unused
+};
+
+struct Bvh {
+    int64_t nt = 0;
+    BNode* nodes = nullptr;        // [nt - 1]
+    float4* tri = nullptr;         // [3 nt] per leaf: (v0, orig idx bits), (e1, 0), (e2, 0)
+    int32_t* leaf_tri = nullptr;   // [nt] original triangle index of each leaf
+    int32_t* leaf_parent = nullptr;// [nt]
+    uint32_t* flags = nullptr;     // [nt] bottom-up visit counters
+    int depth = 0;
+    bool built = false;
+};
+
+// Ring of event pairs per stage; summed (and emptied) by rtsdf_get_stats.
+constexpr int TIMER_RING = 128;
+struct Timer {
+    cudaEvent_t a[TIMER_RING] = {}, b[TIMER_RING] = {};
+    int n = 0;          // recorded pairs not yet summed
+    float carry_ms = 0; // sums of pairs drained early (ring full)
+    int carry_calls = 0;
+};
+
+enum Stage { ST_VOX, ST_JFA, ST_MASK, ST_TRACE, ST_BVH, ST_SHADOW, ST_SHADOW_BWD, ST_MOTION, ST_COUNT };
+
+// tracer work counters (device): rays, node visits, triangle tests
+struct TraceCounters {
+    unsigned long long rays, visits, tests;
+};
+
+}  // namespace rtsdf
+
+struct rtsdf_ctx {
+    rtsdf_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nc = 0, nf = 0;
+    size_t nc3 = 0, nf3 = 0;
+    float hc = 0.f, hf = 0.f;
+
+    // mesh
+    float* verts = nullptr;       // [nv * 3] current positions
+    int32_t* qverts = nullptr;    // [nv * 3] quantised positions
+    int32_t* tris = nullptr;      // [nt * 3]
+    int64_t nv = 0, nt = 0, cap_v = 0, cap_t = 0;
+    bool have_mesh = false;
+
+    // rigid objects
+    int32_t* vert_obj = nullptr;  // [nv]
+    int n_obj = 0, cap_obj = 0;
+    float* obj_box = nullptr;     // [n_obj * 6] box before the last move (lo xyz, hi xyz)
+    float* obj_trans = nullptr;   // [n_obj * 3]
+    int32_t* moved_list = nullptr;// [n_obj] objects with a non-zero translation
+    int32_t* d_moved_count = nullptr;
+    bool reset_pending = false;
+
+    // coarse grid
+    uint32_t* seeds[2] = {nullptr, nullptr};
+    int cur = 0;                  // seeds[cur] holds the latest result
+    float* coarse = nullptr;
+    bool voxelized = false, flooded = false;
+    int jfa_passes = 0;
+
+    // voxelization work list of large triangles
+    int32_t* big_list = nullptr;
+    uint32_t* d_big_count = nullptr;
+
+    // fine grid
+    float* accum = nullptr;
+    uint32_t* counts = nullptr;
+    float* fine = nullptr;
+    uint32_t* masked = nullptr;   // masked coarse voxels
+    uint32_t* d_masked_count = nullptr;
+    int64_t last_masked = -1;
+
+    rtsdf::Bvh bvh;
+    bool bvh_dirty = true;
+
+    uint32_t* d_err = nullptr;
+    int64_t launches = 0;
+    bool profiling = false;
+    bool counting = false;
+    rtsdf::TraceCounters* d_counters = nullptr;
+    rtsdf::Timer timers[rtsdf::ST_COUNT];
+};
+
+namespace rtsdf {
+
+// Launch helpers (count every kernel this context launches).
+#define RTSDF_LAUNCH(ctx, kern, grid, block, smem, ...)                       \
+    do {                                                                      \
+        kern<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);        \
+        (ctx)->launches++;                                                    \
+    } while (0)
+
+// Stage launchers, one per translation unit; each returns a cudaError_t of
+// the launches (cudaGetLastError), never synchronises.
+cudaError_t launch_quantise(rtsdf_ctx* c);
+cudaError_t launch_validate_tris(rtsdf_ctx* c);
+cudaError_t launch_voxelize(rtsdf_ctx* c);
+cudaError_t launch_jfa(rtsdf_ctx* c);
+cudaError_t launch_mask(rtsdf_ctx* c, float d_vox);
+cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame);
+cudaError_t launch_bvh_build(rtsdf_ctx* c);
+cudaError_t launch_bvh_refit(rtsdf_ctx* c);
+cudaError_t launch_move(rtsdf_ctx* c);
+cudaError_t launch_shadow(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm,
+                          int64_t npix, const float L[3], float k, int steps, float smax,
+                          float eps, float* vis);
+cudaError_t launch_shadow_bwd(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm,
+                              int64_t npix, const float L[3], float inv_norm, float k, int steps,
+                              float smax, float eps, const float* dvis, float* dsdf,
+                              float* dlight);
+
+// Mask threshold T = floor((d + beta)^2) in coarse voxels (-1: nothing masked).
+int64_t mask_threshold(float d_vox, float beta_vox);
+
+}  // namespace rtsdf

@@ -1,0 +1,158 @@
+"""GPU parity of Sec. 2.2 (Philox directions, BVH closest-hit tracing, Eq. 1
+accumulation, the front/back sign vote, the reset in changed regions).
+
+Bar: per traced texel |u_gpu - u_oracle| <= 2e-5 x scene diagonal, and the
+front/back counts equal, except on texels where a grazing hit decides
+differently -- those are counted and must stay below 1e-4 of the texels.
+Both sides take the hit decisions in fp32 with the same operation order,
+so in practice the results are identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import scenes as S
+from tests._util import child_texels
+
+pytestmark = pytest.mark.gpu
+
+BMIN = np.zeros(3, np.float32)
+DIAG = np.sqrt(3.0)
+TOL = 2e-5 * DIAG
+
+
+def _compare(rt, pipe, texels, label):
+    g = rt.grids()
+    u = g["accum"].cpu().numpy().astype(np.float64)
+    cnt = g["counts"].cpu().numpy().astype(np.int64)
+    f = g["fine"].cpu().numpy().astype(np.float64)
+    tx = pipe.texels() if texels is None else texels
+    idx = np.arange(tx.size) if texels is None else np.arange(texels.size)
+    ug, uo = u[tx], pipe.u[idx]
+    nfg, nbg = cnt[tx] & 0xFFFF, cnt[tx] >> 16
+    fg, fo = f[tx], pipe.f[idx]
+    both_inf = np.isinf(ug) & np.isinf(uo)
+    with np.errstate(invalid="ignore"):
+        du = np.where(both_inf, 0.0, np.abs(ug - uo))
+    bad = (du > TOL) | (nfg != pipe.nF[idx]) | (nbg != pipe.nB[idx]) | (np.abs(fg - fo) > TOL)
+    rate = bad.mean() if bad.size else 0.0
+    exact = np.mean((ug == uo) | both_inf) if bad.size else 1.0
+    print(f"{label}: texels={tx.size} mismatched={bad.sum()} ({rate:.2e}) u-exact={exact:.6f}")
+    assert rate <= 1e-4, (label, bad.sum(), tx.size)
+    return exact
+
+
+@pytest.mark.parametrize("R", [1, 4, 16, 64])
+def test_tiny_scene_all_texels_over_frames(R):
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.tiny_scene()
+    nc, d, beta = 32, 2.0, 0.5
+    rt = RTSDF(nc, beta_vox=beta, seed=0)
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 0)
+    frames = 4 if R <= 16 else 2
+    for t in range(frames):
+        rt.update(d, R, t)
+        pipe.frame(m.verts, m.tris, t, R)
+    rt.sync()
+    _compare(rt, pipe, None, f"tiny R={R}")
+    # the fine grid everywhere (masked and unmasked texels)
+    f = rt.grids()["fine"].cpu().numpy().astype(np.float64)
+    fin = np.isfinite(pipe.f)
+    assert np.array_equal(fin, np.isfinite(f))
+    assert np.max(np.abs(f[fin] - pipe.f[fin])) <= TOL
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.5])
+def test_eq1_decay(alpha):
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.tiny_scene()
+    nc, d, beta, R = 16, 2.0, 0.5, 8
+    rt = RTSDF(nc, beta_vox=beta, alpha=alpha, seed=5)
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, alpha, 5)
+    for t in range(3):
+        rt.update(d, R, t)
+        pipe.frame(m.verts, m.tris, t, R)
+    rt.sync()
+    g = rt.grids()
+    tx = pipe.texels()
+    m_ = np.isfinite(pipe.u)
+    u = g["accum"].cpu().numpy().astype(np.float64)[tx]
+    assert np.array_equal(np.isfinite(u), m_)
+    assert np.max(np.abs(u[m_] - pipe.u[m_])) <= 1e-6
+
+
+def test_room_sampled_texels():
+    # procedural room (~100k triangles) at 128^3 -> 256^3, 64 rays, 2 frames;
+    # the oracle traces a seeded sample of the masked texels by brute force
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.room_scene(1)
+    nc, d, beta, R = 128, 2.0, 0.5, 64
+    rt = RTSDF(nc, beta_vox=beta, seed=1)
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    for t in range(2):
+        rt.update(d, R, t)
+    rt.sync()
+    n_m = rt.masked_count()
+    masked = rt.grids()["masked"].cpu().numpy()[:n_m]
+    tex = child_texels(masked, nc)
+    sample = np.sort(np.random.default_rng(11).choice(tex, 96, replace=False))
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 1, track=sample)
+    for t in range(2):
+        pipe.frame(m.verts, m.tris, t, R)
+    _compare(rt, pipe, sample, "room sample")
+
+
+def test_motion_refit_and_reset():
+    from paper_2210_04449_gb300 import RTSDF
+    mesh = S.animated_scene(4, n_objects=12, n_lon=16, n_lat=9)
+    nc, d, beta, R = 32, 2.0, 0.5, 8
+    rt = RTSDF(nc, beta_vox=beta, seed=9)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.set_objects(mesh.vert_object, mesh.n_objects)
+    rt.build_bvh()
+    verts = mesh.verts.copy()
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 9)
+    moved = None
+    for t in range(4):
+        if t > 0:
+            tr = S.object_translations(4, t, mesh.n_objects, 0.5 / nc)
+            tr[::3] = 0.0                                     # some objects stay put
+            lo = np.stack([verts[mesh.vert_object == k].min(0) for k in range(mesh.n_objects)])
+            hi = np.stack([verts[mesh.vert_object == k].max(0) for k in range(mesh.n_objects)])
+            mv = np.any(tr != 0, axis=1)
+            moved = (lo[mv], hi[mv])
+            verts = (verts + tr[mesh.vert_object]).astype(np.float32)
+            rt.move_objects(tr)
+            rt.build_bvh(refit=True)
+        rt.update(d, R, t)
+        pipe.frame(verts, mesh.tris, t, R, moved_aabbs=moved)
+    rt.sync()
+    _compare(rt, pipe, None, "motion")
+
+
+def test_checkpoint_resume_is_bit_identical():
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.tiny_scene()
+    nc, d, R = 16, 2.0, 8
+    a = RTSDF(nc, seed=3)
+    a.upload_mesh(m.verts, m.tris)
+    a.build_bvh()
+    for t in range(2):
+        a.update(d, R, t)
+    state = a.save_state()
+    for t in range(2, 4):
+        a.update(d, R, t)
+    b = RTSDF(nc, seed=3)
+    b.upload_mesh(m.verts, m.tris)
+    b.build_bvh()
+    b.load_state(state)
+    for t in range(2, 4):
+        b.update(d, R, t)
+    ga, gb = a.grids(), b.grids()
+    for k in ("accum", "counts", "fine"):
+        assert np.array_equal(ga[k].cpu().numpy(), gb[k].cpu().numpy()), k
