@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--impl", default="rtsdf", choices=["rtsdf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--objects", type=int, default=N_OBJ, help="sphere count (500 = the 1M-triangle workload)")
+    ap.add_argument("--coarse-n", type=int, default=NC, help="coarse grid size (256 = the benchmark workload; "
+                                                              "smaller only for profiling captures)")
     return ap.parse_args()
 
 
@@ -132,11 +134,12 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(dev)
     mesh = S.animated_scene(SEED, n_objects=args.objects)
     n_frames = args.warmup + args.steps
-    trans = np.stack([S.object_translations(SEED, t, mesh.n_objects, 0.5 / NC) for t in range(n_frames + 1)])
+    nc = args.coarse_n
+    trans = np.stack([S.object_translations(SEED, t, mesh.n_objects, 0.5 / nc) for t in range(n_frames + 1)])
     trans_dev = torch.tensor(trans, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    rt = RTSDF(NC, beta_vox=BETA, seed=SEED)
+    rt = RTSDF(nc, beta_vox=BETA, seed=SEED)
     rt.upload_mesh(mesh.verts, mesh.tris)
     rt.set_objects(mesh.vert_object, mesh.n_objects)
     rt.build_bvh()
@@ -210,8 +213,8 @@ def run_gpu(args, rank, world):
     rays_frame = n_masked_tex * RAYS
     trace_ms = stage["trace"]
     jfa_ms = stage["jfa"]
-    passes = math.ceil(math.log2(NC))
-    jfa_bytes = passes * NC ** 3 * 8 + NC ** 3 * 4
+    passes = math.ceil(math.log2(nc))
+    jfa_bytes = passes * nc ** 3 * 8 + nc ** 3 * 4
     jfa_gbs = jfa_bytes / (jfa_ms * 1e-3) / 1e9 if jfa_ms else None
 
     peaks = {}
@@ -246,9 +249,10 @@ def run_gpu(args, rank, world):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded procedural scene: 500 displaced UV spheres, random rigid motion)",
-        "config": {"workload": "animated 256^3->512^3, 500 spheres / 1,000,000 tris, 64 rays/texel, "
-                               "d=2 voxels, beta=0.5, reset in changed regions, per-frame refit+voxelize+JFA",
-                   "coarse_n": NC, "fine_n": 2 * NC, "triangles": int(mesh.nt), "rays_per_texel": RAYS,
+        "config": {"workload": f"animated {nc}^3->{2 * nc}^3, {mesh.n_objects} spheres / {mesh.nt:,} tris, "
+                               "64 rays/texel, d=2 voxels, beta=0.5, reset in changed regions, "
+                               "per-frame refit+voxelize+JFA",
+                   "coarse_n": nc, "fine_n": 2 * nc, "triangles": int(mesh.nt), "rays_per_texel": RAYS,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (fine grids 3 x 512 MB)"},
         "gpu_launches": int(launches),
