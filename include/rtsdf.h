@@ -183,6 +183,26 @@ rtsdf_status rtsdf_shadow_backward(rtsdf_t ctx, const float* sdf, const float* p
                                    int32_t steps, float step_max_vox, float eps_vox,
                                    const float* dvis, float* dsdf, float* dlight);
 
+/* Jump flooding into caller buffers with no device allocation at all.
+ * (Not a step of the paper: an alternative entry point to rtsdf_jfa.)
+ * For hosts that cannot call cudaMalloc -- a plug-in running inside another
+ * application's memory budget, or a frame loop that bans allocations after
+ * start-up because allocating can synchronise the device.  The result equals
+ * rtsdf_jfa's: seeds_in is a voxelized seed grid (packed as in rtsdf_grids,
+ * 0xFFFFFFFF = no seed), seeds_out receives the nearest seed of every voxel
+ * and coarse_out the coarse SDF (h_c = extent / n, beta in coarse voxels);
+ * all three are caller-owned device buffers of n^3 elements that must not
+ * overlap.  The only scratch is a fixed 8 MiB array inside the library
+ * (n <= 128; larger n returns RTSDF_E_ARG), which every GPU that loads the
+ * library keeps until the process exits.  The first call on a device looks
+ * up that array's address (once per device; make this first call before any
+ * stream capture).  All calls share the array: two calls that overlap on the
+ * GPU (e.g. on different streams) race and both results are undefined.
+ * Work is enqueued on `stream` (NULL = legacy default stream); launch errors
+ * return RTSDF_E_CUDA. */
+rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* seeds_out, float* coarse_out,
+                               int32_t n, float extent, float beta_vox, void* stream);
+
 /* Borrowed device views of the grids (no synchronisation). */
 rtsdf_status rtsdf_get_grids(rtsdf_t ctx, rtsdf_grids* out);
 

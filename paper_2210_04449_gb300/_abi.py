@@ -56,6 +56,7 @@ SIGNATURES = {
     "rtsdf_shadow": (status_t, [ctx_t, c_vp, c_vp, c_vp, c_i64, F3, c_f, c_i32, c_f, c_f, c_vp]),
     "rtsdf_shadow_backward": (status_t, [ctx_t, c_vp, c_vp, c_vp, c_i64, F3, c_f, c_i32, c_f, c_f, c_vp, c_vp,
                                          c_vp]),
+    "rtsdf_jfa_noalloc": (status_t, [c_vp, c_vp, c_vp, c_i32, c_f, c_f, c_vp]),
     "rtsdf_get_grids": (status_t, [ctx_t, ctypes.POINTER(Grids)]),
     "rtsdf_get_masked_count": (status_t, [ctx_t, ctypes.POINTER(c_i64)]),
     "rtsdf_get_stats": (status_t, [ctx_t, ctypes.POINTER(Stats)]),

@@ -11,7 +11,10 @@
 // and "no seed" (all ones) is pushed above every real distance by OR-ing
 // the seed's top byte into D2.  The candidate key is then the pair
 // (D2, seed), compared lexicographically.
+#include <math.h>
 #include <math_constants.h>
+
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -106,4 +109,95 @@ cudaError_t launch_jfa(rtsdf_ctx* c) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free jump flood (rtsdf_jfa_noalloc).
+//
+// Hosts that manage every byte of device memory themselves -- an engine
+// plug-in living inside another application's memory budget, or a render
+// loop that forbids allocations after start-up because cudaMalloc/cudaFree
+// can synchronise the device -- cannot let the library allocate.  This entry
+// point runs the same passes as rtsdf_jfa on caller buffers; its only
+// scratch (the second ping-pong grid) is the fixed array below, which every
+// GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int NOALLOC_MAX_N = 128;             // 128^3 x 4 B = 8 MiB of scratch
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) uint32_t g_jfa_scratch[NOALLOC_MAX_N * NOALLOC_MAX_N * NOALLOC_MAX_N];
+
+std::mutex g_scratch_mutex;
+uint32_t* g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress with that device current).
+cudaError_t scratch_for_current_device(uint32_t** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_jfa_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void k_copy_u32(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, size_t n) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+}  // namespace
+
 }  // namespace rtsdf
+
+extern "C" rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* seeds_out, float* coarse_out,
+                                          int32_t n, float extent, float beta_vox, void* stream) {
+    using namespace rtsdf;
+    if (!seeds_in || !seeds_out || !coarse_out) return RTSDF_E_ARG;
+    if (n < 1 || n > NOALLOC_MAX_N) return RTSDF_E_ARG;
+    if (!(extent > 0.f) || !isfinite(extent) || !(beta_vox >= 0.f) || !isfinite(beta_vox)) return RTSDF_E_ARG;
+    const size_t n3 = (size_t)n * n * n;
+    if (overlaps(seeds_in, n3 * 4, seeds_out, n3 * 4) || overlaps(seeds_in, n3 * 4, coarse_out, n3 * 4) ||
+        overlaps(seeds_out, n3 * 4, coarse_out, n3 * 4))
+        return RTSDF_E_ARG;
+    uint32_t* scratch = nullptr;
+    if (scratch_for_current_device(&scratch) != cudaSuccess) return RTSDF_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float hc = extent / (float)n;
+    const float beta_h = beta_vox * hc;
+    int L = 0;
+    while ((1 << L) < n) L++;
+    if (L == 0) {
+        k_copy_u32<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(seeds_in, seeds_out, n3);
+        k_coarse_only<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(seeds_in, n3, n, coarse_out, hc, beta_h);
+    } else {
+        // pass i (1-based, L passes) writes seeds_out when L - i is even, else
+        // the scratch array, so the last pass lands in seeds_out
+        dim3 block(32, 8, 1), grid((n + 31) / 32, (n + 7) / 8, n);
+        const uint32_t* in = seeds_in;
+        for (int i = 1; i <= L; i++) {
+            const int k = 1 << (L - i);
+            uint32_t* out = ((L - i) % 2 == 0) ? seeds_out : scratch;
+            if (i == L)
+                k_jfa_pass<true><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
+            else
+                k_jfa_pass<false><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
+            in = out;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? RTSDF_OK : RTSDF_E_CUDA;
+}
