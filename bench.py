@@ -38,11 +38,11 @@ NC, D_VOX, BETA, RAYS, SEED = 256, 2.0, 0.5, 64, 2
 N_OBJ = 500
 
 # fp32 pipe operations per BVH node entered / per ray-triangle test in the
-# tracer's source (fma counted as 2 flops): two slab tests of 6 fma + 15
-# min/max/compare each, one ordering compare; Moller-Trumbore: 3 crosses
-# (3 fma + 3 mul each), 4 dots (2 fma + 1 mul), 3 subtracts, 1 divide
-# (counted as 1), 3 scales, 1 add and 5 compares.
-FLOP_PER_VISIT = 2 * (6 * 2 + 15) + 1
+# tracer's source (fma counted as 2 flops): a 4-wide node is four slab tests
+# of 6 fma + 12 min/max + 1 compare and a 5-exchange sort; Moller-Trumbore:
+# 3 crosses (3 fma + 3 mul each), 4 dots (2 fma + 1 mul), 3 subtracts,
+# 1 divide (counted as 1), 3 scales, 1 add and 5 compares.
+FLOP_PER_VISIT = 4 * (6 * 2 + 12 + 1) + 5
 FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed

@@ -74,7 +74,9 @@ void free_all(rtsdf_ctx* c) {
     dfree(c->obj_trans); dfree(c->moved_list); dfree(c->d_moved_count);
     dfree(c->seeds[0]); dfree(c->seeds[1]); dfree(c->coarse); dfree(c->big_list); dfree(c->d_big_count);
     dfree(c->accum); dfree(c->counts); dfree(c->fine); dfree(c->masked); dfree(c->d_masked_count);
-    dfree(c->bvh.nodes); dfree(c->bvh.tri); dfree(c->bvh.leaf_tri); dfree(c->bvh.leaf_parent); dfree(c->bvh.flags);
+    dfree(c->ray_min); dfree(c->ray_cnt); dfree(c->d_next_ray);
+    dfree(c->bin_count); dfree(c->bin_start); dfree(c->bin_cursor); dfree(c->bin_items); dfree(c->bin_overflow);
+    dfree(c->bvh.nodes); dfree(c->bvh.wide); dfree(c->bvh.nbox); dfree(c->bvh.lbox); dfree(c->bvh.tri); dfree(c->bvh.leaf_tri); dfree(c->bvh.leaf_parent); dfree(c->bvh.flags);
     dfree(c->d_err);
     dfree(c->d_counters);
     for (auto& t : c->timers) {
@@ -177,6 +179,19 @@ rtsdf_status rtsdf_create(const rtsdf_config* cfg, rtsdf_t* out) {
     if (!e) e = dalloc(&c->counts, c->nf3);
     if (!e) e = dalloc(&c->fine, c->nf3);
     if (!e) e = dalloc(&c->masked, c->nc3);
+    if (!e) e = dalloc(&c->ray_min, 8 * c->nc3);
+    if (!e) e = dalloc(&c->ray_cnt, 8 * c->nc3);
+    if (!e) e = dalloc(&c->d_next_ray, 1);
+    {
+        const size_t g = (size_t)(c->nc + 7) / 8, cells = g * g * g;
+        c->bin_cap = 1u << 23;
+        if (!e) e = dalloc(&c->bin_count, cells);
+        if (!e) e = dalloc(&c->bin_start, cells + 1);
+        if (!e) e = dalloc(&c->bin_cursor, cells);
+        if (!e) e = dalloc(&c->bin_items, (size_t)c->bin_cap);
+        if (!e) e = dalloc(&c->bin_overflow, 1);
+        if (!e) e = cudaMemsetAsync(c->bin_overflow, 0, sizeof(uint32_t), c->stream);
+    }
     if (!e) e = dalloc(&c->d_masked_count, 1);
     if (!e) e = dalloc(&c->d_big_count, 1);
     if (!e) e = dalloc(&c->d_moved_count, 1);
@@ -189,6 +204,8 @@ rtsdf_status rtsdf_create(const rtsdf_config* cfg, rtsdf_t* out) {
     if (!e) e = cudaMemsetAsync(c->seeds[0], 0xFF, c->nc3 * sizeof(uint32_t), c->stream);
     if (!e) e = cudaMemsetAsync(c->seeds[1], 0xFF, c->nc3 * sizeof(uint32_t), c->stream);
     if (!e) e = fill_f32(c, c->coarse, c->nc3, INFINITY);
+    if (!e) e = fill_f32(c, reinterpret_cast<float*>(c->ray_min), 8 * c->nc3, INFINITY);
+    if (!e) e = cudaMemsetAsync(c->ray_cnt, 0, 8 * c->nc3 * sizeof(uint32_t), c->stream);
     if (!e) e = reset_temporal(c);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) {

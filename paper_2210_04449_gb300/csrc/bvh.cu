@@ -14,6 +14,9 @@
 // Also here: the rigid per-object motion of animated scenes.
 #include <math_constants.h>
 
+#include <utility>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace rtsdf {
@@ -186,8 +189,9 @@ __device__ __forceinline__ void store_child(BNode* node, bool right, const float
 
 // Leaf data + bottom-up boxes.  One thread per leaf.
 __global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __restrict__ tris,
-                            const int32_t* order, int64_t n, float4* __restrict__ tri, int32_t* leaf_tri, const int32_t* __restrict__ leaf_parent,
-                            BNode* nodes, uint32_t* flags, float pad) {
+                            const int32_t* order, int64_t n, float4* __restrict__ tri, int32_t* leaf_tri,
+                            const int32_t* __restrict__ leaf_parent, BNode* nodes, uint32_t* flags, float pad,
+                            float* __restrict__ lbox, float* __restrict__ nbox) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t t = order[i];
@@ -204,6 +208,8 @@ __global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __re
     for (int a = 0; a < 3; a++) {
         lo[a] = pad_lo(fminf(v0[a], fminf(v1[a], v2[a])), pad);
         hi[a] = pad_hi(fmaxf(v0[a], fmaxf(v1[a], v2[a])), pad);
+        lbox[6 * i + a] = lo[a];
+        lbox[6 * i + 3 + a] = hi[a];
     }
     int child = ~(int)i;
     int node = leaf_parent[i];
@@ -222,9 +228,34 @@ __global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __re
         lo[0] = fminf(a[0], b[0]); hi[0] = fmaxf(a[1], b[1]);
         lo[1] = fminf(a[2], b[2]); hi[1] = fmaxf(a[3], b[3]);
         lo[2] = fminf(c[0], c[2]); hi[2] = fmaxf(c[1], c[3]);
+        for (int k = 0; k < 3; k++) {
+            nbox[6 * (int64_t)node + k] = lo[k];
+            nbox[6 * (int64_t)node + 3 + k] = hi[k];
+        }
         child = node;
         node = nd->d.z;
     }
+}
+
+// Child boxes of the 4-wide nodes from the (re)fitted binary boxes.
+__global__ void k_wide_boxes(WNode* __restrict__ wide, int64_t n_wide, const float* __restrict__ nbox,
+                             const float* __restrict__ lbox) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_wide * 4) return;
+    const int64_t w = i >> 2;
+    const int k = (int)(i & 3);
+    const int src = (&wide[w].src.x)[k];
+    float b[6] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F};
+    if (src != WIDE_EMPTY) {
+        const float* p = src >= 0 ? nbox + 6 * (int64_t)src : lbox + 6 * (int64_t)(~src);
+        for (int a = 0; a < 6; a++) b[a] = p[a];
+    }
+    (&wide[w].lox.x)[k] = b[0];
+    (&wide[w].hix.x)[k] = b[3];
+    (&wide[w].loy.x)[k] = b[1];
+    (&wide[w].hiy.x)[k] = b[4];
+    (&wide[w].loz.x)[k] = b[2];
+    (&wide[w].hiz.x)[k] = b[5];
 }
 
 __global__ void k_depth(const int32_t* __restrict__ leaf_parent, const BNode* __restrict__ nodes, int64_t n,
@@ -291,11 +322,84 @@ __global__ void k_translate(float* __restrict__ verts, const int32_t* __restrict
 
 }  // namespace
 
+// Collapse the binary tree into 4-wide nodes (host side, once per build):
+// starting from a binary node's two children, the internal child with the
+// largest surface area is replaced by its two children until four are
+// collected (or only leaves remain); each internal child becomes a wide node.
+static cudaError_t collapse_wide(rtsdf_ctx* c) {
+    Bvh& b = c->bvh;
+    const int64_t n = b.nt;
+    std::vector<BNode> bn((size_t)(n - 1));
+    std::vector<float> box((size_t)(n - 1) * 6);
+    cudaError_t e = cudaMemcpyAsync(bn.data(), b.nodes, sizeof(BNode) * (n - 1), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(box.data(), b.nbox, sizeof(float) * 6 * (n - 1), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    auto area = [&](int node) {
+        const float* p = &box[6 * (size_t)node];
+        const float dx = p[3] - p[0], dy = p[4] - p[1], dz = p[5] - p[2];
+        return dx * dy + dy * dz + dz * dx;
+    };
+    std::vector<WNode> wide;
+    wide.reserve((size_t)(n / 2 + 1));
+    std::vector<std::pair<int, int>> todo;   // (binary node, wide slot)
+    wide.emplace_back();
+    todo.emplace_back(0, 0);
+    for (size_t q = 0; q < todo.size(); q++) {
+        const int bnode = todo[q].first, w = todo[q].second;
+        int kids[4] = {bn[bnode].d.x, bn[bnode].d.y, 0, 0};
+        int nk = 2;
+        while (nk < 4) {
+            int best = -1;
+            float ba = -1.f;
+            for (int k = 0; k < nk; k++)
+                if (kids[k] >= 0 && area(kids[k]) > ba) {
+                    ba = area(kids[k]);
+                    best = k;
+                }
+            if (best < 0) break;
+            const int open = kids[best];
+            kids[best] = bn[open].d.x;
+            kids[nk++] = bn[open].d.y;
+        }
+        int child[4], src[4];
+        for (int k = 0; k < 4; k++) {
+            if (k >= nk) {
+                child[k] = WIDE_EMPTY;
+                src[k] = WIDE_EMPTY;
+                continue;
+            }
+            src[k] = kids[k];
+            if (kids[k] >= 0) {
+                child[k] = (int)wide.size();
+                wide.emplace_back();
+                todo.emplace_back(kids[k], child[k]);
+            } else {
+                child[k] = kids[k];   // ~leaf
+            }
+        }
+        wide[(size_t)w].child = make_int4(child[0], child[1], child[2], child[3]);
+        wide[(size_t)w].src = make_int4(src[0], src[1], src[2], src[3]);
+    }
+    if (b.wide) cudaFree(b.wide);
+    b.wide = nullptr;
+    b.n_wide = (int64_t)wide.size();
+    if ((e = cudaMalloc(&b.wide, sizeof(WNode) * wide.size()))) return e;
+    if ((e = cudaMemcpyAsync(b.wide, wide.data(), sizeof(WNode) * wide.size(), cudaMemcpyHostToDevice, c->stream)))
+        return e;
+    RTSDF_LAUNCH(c, k_wide_boxes, (unsigned)((4 * b.n_wide + 255) / 256), 256, 0, b.wide, b.n_wide, b.nbox, b.lbox);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
+    return e;
+}
+
 cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     Bvh& b = c->bvh;
     const int64_t n = c->nt;
     b.nt = n;
     b.built = false;
+    b.n_wide = 0;
     if (n == 0) {
         b.depth = 0;
         b.built = true;
@@ -314,6 +418,8 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     if ((e = realloc_if((void**)&b.leaf_tri, sizeof(int32_t) * (size_t)n))) return e;
     if ((e = realloc_if((void**)&b.leaf_parent, sizeof(int32_t) * (size_t)n))) return e;
     if ((e = realloc_if((void**)&b.flags, sizeof(uint32_t) * (size_t)n))) return e;
+    if ((e = realloc_if((void**)&b.lbox, sizeof(float) * 6 * (size_t)n))) return e;
+    if ((e = realloc_if((void**)&b.nbox, sizeof(float) * 6 * (size_t)(n > 1 ? n - 1 : 1)))) return e;
     uint32_t *k0 = nullptr, *k1 = nullptr, *hist = nullptr;
     int32_t *v0 = nullptr, *v1 = nullptr, *depth = nullptr;
     if ((e = cudaMalloc(&k0, sizeof(uint32_t) * n)) || (e = cudaMalloc(&k1, sizeof(uint32_t) * n)) ||
@@ -341,9 +447,17 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, c->stream);
     const float pad = c->cfg.extent * 0x1p-16f;
     RTSDF_LAUNCH(c, k_leaves_up, g, 256, 0, c->verts, c->tris, vin, n, b.tri, b.leaf_tri, b.leaf_parent, b.nodes,
-                 b.flags, pad);
+                 b.flags, pad, b.lbox, b.nbox);
     cudaMemsetAsync(depth, 0, sizeof(int32_t), c->stream);
     RTSDF_LAUNCH(c, k_depth, g, 256, 0, b.leaf_parent, b.nodes, n, depth);
+    if (n > 1) {
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = collapse_wide(c);
+        if (e != cudaSuccess) {
+            cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(depth);
+            return e;
+        }
+    }
     e = cudaGetLastError();
     int32_t hd = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hd, depth, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -363,7 +477,9 @@ cudaError_t launch_bvh_refit(rtsdf_ctx* c) {
     if (e != cudaSuccess) return e;
     const float pad = c->cfg.extent * 0x1p-16f;
     RTSDF_LAUNCH(c, k_leaves_up, (unsigned)((n + 255) / 256), 256, 0, c->verts, c->tris, b.leaf_tri, n, b.tri,
-                 b.leaf_tri, b.leaf_parent, b.nodes, b.flags, pad);
+                 b.leaf_tri, b.leaf_parent, b.nodes, b.flags, pad, b.lbox, b.nbox);
+    if (b.n_wide > 0)
+        RTSDF_LAUNCH(c, k_wide_boxes, (unsigned)((4 * b.n_wide + 255) / 256), 256, 0, b.wide, b.n_wide, b.nbox, b.lbox);
     return cudaGetLastError();
 }
 

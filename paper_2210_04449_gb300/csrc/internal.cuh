@@ -38,9 +38,24 @@ struct __align__(16) BNode {
     int4 d;     // left, right, parent, unused
 };
 
+// 4-wide node collapsed from the binary tree: child boxes SoA (one float4
+// per plane), child ids (>= 0 wide node, < 0 ~leaf), and for the refit the
+// binary source of every child (>= 0 binary node, < 0 ~leaf, WIDE_EMPTY = no
+// child; an empty slot has lo = +inf, hi = -inf and never hits).
+constexpr int WIDE_EMPTY = (int)0x80000000;
+struct __align__(16) WNode {
+    float4 lox, hix, loy, hiy, loz, hiz;
+    int4 child;
+    int4 src;
+};
+
 struct Bvh {
     int64_t nt = 0;
     BNode* nodes = nullptr;        // [nt - 1]
+    WNode* wide = nullptr;         // [n_wide]
+    int64_t n_wide = 0;
+    float* nbox = nullptr;         // [nt - 1][6] box of every binary node
+    float* lbox = nullptr;         // [nt][6] padded box of every leaf
     float4* tri = nullptr;         // [3 nt] per leaf: (v0, orig idx bits), (e1, 0), (e2, 0)
     int32_t* leaf_tri = nullptr;   // [nt] original triangle index of each leaf
     int32_t* leaf_parent = nullptr;// [nt]
@@ -90,6 +105,13 @@ struct rtsdf_ctx {
     int32_t* moved_list = nullptr;// [n_obj] objects with a non-zero translation
     int32_t* d_moved_count = nullptr;
     bool reset_pending = false;
+    // moved boxes binned on a coarse cell grid for the reset test
+    uint32_t* bin_count = nullptr;
+    uint32_t* bin_start = nullptr;
+    uint32_t* bin_cursor = nullptr;
+    int32_t* bin_items = nullptr;
+    uint32_t* bin_overflow = nullptr;
+    uint32_t bin_cap = 0;
 
     // coarse grid
     uint32_t* seeds[2] = {nullptr, nullptr};
@@ -109,6 +131,14 @@ struct rtsdf_ctx {
     uint32_t* masked = nullptr;   // masked coarse voxels
     uint32_t* d_masked_count = nullptr;
     int64_t last_masked = -1;
+
+    // tracer scratch: per texel slot (8 per masked voxel) this frame's
+    // smallest hit distance (float bits, +inf = none) and front | back << 16
+    // hit counts; cleared again by the finalize kernel
+    uint32_t* ray_min = nullptr;
+    uint32_t* ray_cnt = nullptr;
+    unsigned long long* d_next_ray = nullptr;
+    unsigned trace_grid = 0;
 
     rtsdf::Bvh bvh;
     bool bvh_dirty = true;

@@ -33,7 +33,13 @@ __device__ __forceinline__ float coarse_value(uint32_t best, uint32_t d2, float 
     return __fsub_rn(__fmul_rn(hc, __fsqrt_rn((float)d2)), beta_h);
 }
 
-// Tiles of 32 x 8 voxels (x, y) per block, one z-plane per grid z.
+// Tiles of 32 x 8 voxels (x, y) per block, one z-plane per grid z.  The 27
+// candidates are read branch-free: an offset that leaves the grid reads the
+// voxel's own coordinate on that axis (always in bounds) and the value is
+// then forced to "no seed".  The arg-min runs in two passes over the 27
+// (D2, seed) pairs kept in registers: the smallest D2 first, then the
+// smallest seed among the candidates at that D2 -- the same result as a
+// lexicographic (D2, seed) minimum.
 template <bool FINAL>
 __global__ void __launch_bounds__(256) k_jfa_pass(const uint32_t* __restrict__ in,
                                                  uint32_t* __restrict__ out, int n, int k,
@@ -44,32 +50,44 @@ __global__ void __launch_bounds__(256) k_jfa_pass(const uint32_t* __restrict__ i
     if (x >= n || y >= n) return;
     const uint32_t v = pack_seed(x, y, z);
     const uint32_t vv = __dp4a(v, v, 0u);
-    uint32_t best = SEED_EMPTY, bestd = 0xFFFFFFFFu;
+    int xs[3], ys[3], zs[3];
+    uint32_t mx[3], my[3], mz[3];   // all ones where the offset leaves the grid
 #pragma unroll
-    for (int iz = -1; iz <= 1; iz++) {
-        const int zz = z + iz * k;
-        if (zz < 0 || zz >= n) continue;
+    for (int i = 0; i < 3; i++) {
+        const int o = (i - 1) * k;
+        const bool okx = x + o >= 0 && x + o < n, oky = y + o >= 0 && y + o < n, okz = z + o >= 0 && z + o < n;
+        xs[i] = okx ? x + o : x;
+        ys[i] = oky ? y + o : y;
+        zs[i] = okz ? z + o : z;
+        mx[i] = okx ? 0u : 0xFFFFFFFFu;
+        my[i] = oky ? 0u : 0xFFFFFFFFu;
+        mz[i] = okz ? 0u : 0xFFFFFFFFu;
+    }
+    uint32_t cs[27], cd[27];
+    uint32_t dmin = 0xFFFFFFFFu;
 #pragma unroll
-        for (int iy = -1; iy <= 1; iy++) {
-            const int yy = y + iy * k;
-            if (yy < 0 || yy >= n) continue;
-            const uint32_t* row = in + (size_t)n * (yy + (size_t)n * zz);
+    for (int iz = 0; iz < 3; iz++) {
 #pragma unroll
-            for (int ix = -1; ix <= 1; ix++) {
-                const int xx = x + ix * k;
-                if (xx < 0 || xx >= n) continue;
-                const uint32_t s = __ldg(row + xx);
-                const uint32_t d = seed_d2(s, v, vv);
-                if (d < bestd || (d == bestd && s < best)) {
-                    bestd = d;
-                    best = s;
-                }
+        for (int iy = 0; iy < 3; iy++) {
+            const uint32_t* row = in + (size_t)n * (ys[iy] + (size_t)n * zs[iz]);
+            const uint32_t mrow = my[iy] | mz[iz];
+#pragma unroll
+            for (int ix = 0; ix < 3; ix++) {
+                const int c = 9 * iz + 3 * iy + ix;
+                const uint32_t sv = __ldg(row + xs[ix]) | mrow | mx[ix];
+                cs[c] = sv;
+                cd[c] = seed_d2(sv, v, vv);
+                dmin = min(dmin, cd[c]);
             }
         }
     }
+    uint32_t best = SEED_EMPTY;
+#pragma unroll
+    for (int c = 0; c < 27; c++)
+        if (cd[c] == dmin) best = min(best, cs[c]);
     const size_t idx = x + (size_t)n * (y + (size_t)n * z);
     out[idx] = best;
-    if (FINAL) coarse[idx] = coarse_value(best, bestd, hc, beta_h);
+    if (FINAL) coarse[idx] = coarse_value(best, dmin, hc, beta_h);
 }
 
 // Coarse SDF without a pass (N = 1: no jump steps).

@@ -27,20 +27,97 @@ int64_t mask_threshold(float d_vox, float beta_vox) {
 
 namespace {
 
-__device__ __forceinline__ bool near_moved_box(float px, float py, float pz, float u,
-                                               const float* __restrict__ boxes,
-                                               const int32_t* __restrict__ moved, int n_moved) {
-    // fp32, fixed order: d = max(max(lo - p, p - hi), 0); d2 = (dx dx + dy dy) + dz dz
-    const float uu = __fmul_rn(u, u);
-    for (int i = 0; i < n_moved; i++) {
-        const float* b = boxes + 6 * moved[i];
-        float dx = fmaxf(fmaxf(__fsub_rn(b[0], px), __fsub_rn(px, b[3])), 0.f);
-        float dy = fmaxf(fmaxf(__fsub_rn(b[1], py), __fsub_rn(py, b[4])), 0.f);
-        float dz = fmaxf(fmaxf(__fsub_rn(b[2], pz), __fsub_rn(pz, b[5])), 0.f);
-        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        if (d2 <= uu) return true;
+// fp32, fixed order: d = max(max(lo - p, p - hi), 0); d2 = (dx dx + dy dy) + dz dz
+__device__ __forceinline__ bool within(const float* __restrict__ b, float px, float py, float pz, float uu) {
+    const float dx = fmaxf(fmaxf(__fsub_rn(b[0], px), __fsub_rn(px, b[3])), 0.f);
+    const float dy = fmaxf(fmaxf(__fsub_rn(b[1], py), __fsub_rn(py, b[4])), 0.f);
+    const float dz = fmaxf(fmaxf(__fsub_rn(b[2], pz), __fsub_rn(pz, b[5])), 0.f);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return d2 <= uu;
+}
+
+// Moved boxes are binned into cells of BIN_VOX^3 coarse voxels, each box
+// dilated by BIN_REACH coarse voxels (+1 cell of slack against rounding).
+// A texel whose accumulated distance u is at most BIN_REACH voxels can only
+// be within u of boxes listed in its own cell; other texels test every
+// moved box.  Both paths apply the same fp32 test, so the result equals the
+// test against all moved boxes.
+constexpr int BIN_VOX = 8;
+constexpr float BIN_REACH = 4.f;
+
+struct BinArgs {
+    const float* boxes;
+    const int32_t* moved;
+    const int32_t* n_moved;
+    int g;                 // cells per axis
+    float bx, by, bz, inv_cell, reach;
+    uint32_t* count;       // [g^3]
+    uint32_t* start;       // [g^3 + 1]
+    uint32_t* cursor;      // [g^3]
+    int32_t* items;
+    uint32_t cap;
+    uint32_t* overflow;
+};
+
+__device__ __forceinline__ void box_cells(const BinArgs& a, const float* b, int lo[3], int hi[3]) {
+    const float o[3] = {a.bx, a.by, a.bz};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        lo[k] = max((int)floorf((b[k] - a.reach - o[k]) * a.inv_cell) - 1, 0);
+        hi[k] = min((int)floorf((b[3 + k] + a.reach - o[k]) * a.inv_cell) + 1, a.g - 1);
     }
-    return false;
+}
+
+__global__ void k_bin_count(BinArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *a.n_moved) return;
+    int lo[3], hi[3];
+    box_cells(a, a.boxes + 6 * a.moved[i], lo, hi);
+    for (int z = lo[2]; z <= hi[2]; z++)
+        for (int y = lo[1]; y <= hi[1]; y++)
+            for (int x = lo[0]; x <= hi[0]; x++) atomicAdd(a.count + x + a.g * (y + a.g * z), 1u);
+}
+
+// exclusive scan of the cell counts (one block); start[g^3] = total
+__global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
+    __shared__ uint32_t part[1024];
+    const int64_t total = (int64_t)a.g * a.g * a.g;
+    const int64_t per = (total + 1023) / 1024;
+    const int64_t lo = threadIdx.x * per, hi = min(lo + per, total);
+    uint32_t s = 0;
+    for (int64_t i = lo; i < hi; i++) s += a.count[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int64_t i = lo; i < hi; i++) {
+        a.start[i] = run;
+        a.cursor[i] = 0;
+        run += a.count[i];
+    }
+    if (threadIdx.x == 1023) {
+        a.start[total] = part[1023];
+        if (part[1023] > a.cap) *a.overflow = 1u;
+    }
+}
+
+__global__ void k_bin_fill(BinArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *a.n_moved || *a.overflow) return;
+    const int obj = a.moved[i];
+    int lo[3], hi[3];
+    box_cells(a, a.boxes + 6 * obj, lo, hi);
+    for (int z = lo[2]; z <= hi[2]; z++)
+        for (int y = lo[1]; y <= hi[1]; y++)
+            for (int x = lo[0]; x <= hi[0]; x++) {
+                const int c = x + a.g * (y + a.g * z);
+                a.items[a.start[c] + atomicAdd(a.cursor + c, 1u)] = obj;
+            }
 }
 
 struct MaskArgs {
@@ -60,7 +137,28 @@ struct MaskArgs {
     const int32_t* n_moved;
     int reset;
     float bx, by, bz, hf;
+    // binned moved boxes
+    const uint32_t* bin_start;
+    const int32_t* bin_items;
+    const uint32_t* bin_overflow;
+    int bin_g;
+    float reach;   // BIN_REACH coarse voxels in world units
 };
+
+__device__ __forceinline__ bool near_moved_box(const MaskArgs& a, int cx, int cy, int cz, float px, float py,
+                                               float pz, float u, int n_moved) {
+    const float uu = __fmul_rn(u, u);
+    if (u <= a.reach && !*a.bin_overflow) {
+        const int c = cx / BIN_VOX + a.bin_g * (cy / BIN_VOX + a.bin_g * (cz / BIN_VOX));
+        const uint32_t e = a.bin_start[c + 1];
+        for (uint32_t i = a.bin_start[c]; i < e; i++)
+            if (within(a.boxes + 6 * a.bin_items[i], px, py, pz, uu)) return true;
+        return false;
+    }
+    for (int i = 0; i < n_moved; i++)
+        if (within(a.boxes + 6 * a.moved[i], px, py, pz, uu)) return true;
+    return false;
+}
 
 __global__ void __launch_bounds__(256) k_mask(MaskArgs a) {
     const int n = a.nc;
@@ -116,7 +214,7 @@ __global__ void __launch_bounds__(256) k_mask(MaskArgs a) {
                     const float px = __fadd_rn(a.bx, __fmul_rn(__fadd_rn((float)(2 * x + dx), 0.5f), a.hf));
                     const float py = __fadd_rn(a.by, __fmul_rn(__fadd_rn((float)(2 * y + dy), 0.5f), a.hf));
                     const float pz = __fadd_rn(a.bz, __fmul_rn(__fadd_rn((float)(2 * z + dz), 0.5f), a.hf));
-                    if (near_moved_box(px, py, pz, un[dx], a.boxes, a.moved, n_moved)) {
+                    if (near_moved_box(a, x, y, z, px, py, pz, un[dx], n_moved)) {
                         un[dx] = CUDART_INF_F;
                         clear[dx] = true;
                     }
@@ -163,6 +261,36 @@ cudaError_t launch_mask(rtsdf_ctx* c, float d_vox) {
     a.by = c->cfg.bmin[1];
     a.bz = c->cfg.bmin[2];
     a.hf = c->hf;
+    a.bin_g = (n + BIN_VOX - 1) / BIN_VOX;
+    a.reach = BIN_REACH * c->hc;
+    a.bin_start = c->bin_start;
+    a.bin_items = c->bin_items;
+    a.bin_overflow = c->bin_overflow;
+    if (a.reset) {
+        BinArgs b;
+        b.boxes = c->obj_box;
+        b.moved = c->moved_list;
+        b.n_moved = c->d_moved_count;
+        b.g = a.bin_g;
+        b.bx = c->cfg.bmin[0];
+        b.by = c->cfg.bmin[1];
+        b.bz = c->cfg.bmin[2];
+        b.inv_cell = 1.f / (BIN_VOX * c->hc);
+        b.reach = a.reach;
+        b.count = c->bin_count;
+        b.start = c->bin_start;
+        b.cursor = c->bin_cursor;
+        b.items = c->bin_items;
+        b.cap = c->bin_cap;
+        b.overflow = c->bin_overflow;
+        const size_t cells = (size_t)b.g * b.g * b.g;
+        if ((e = cudaMemsetAsync(c->bin_count, 0, cells * sizeof(uint32_t), c->stream))) return e;
+        if ((e = cudaMemsetAsync(c->bin_overflow, 0, sizeof(uint32_t), c->stream))) return e;
+        const unsigned gb = (unsigned)((c->n_obj + 127) / 128);
+        RTSDF_LAUNCH(c, k_bin_count, gb, 128, 0, b);
+        RTSDF_LAUNCH(c, k_bin_scan, 1, 1024, 0, b);
+        RTSDF_LAUNCH(c, k_bin_fill, gb, 128, 0, b);
+    }
     dim3 block(32, 8, 1), grid((n + 31) / 32, (n + 7) / 8, n);
     RTSDF_LAUNCH(c, k_mask, grid, block, 0, a);
     c->reset_pending = false;

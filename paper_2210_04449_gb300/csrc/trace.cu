@@ -1,24 +1,28 @@
 // Sec. 2.2 -- ray tracing of the masked fine texels with temporal
 // accumulation (Eq. 1) and the front/back sign vote.
 //
-// Work layout: the mask kernel lists masked coarse voxels; each contributes
-// its 8 fine children.  A group of G = min(R, 32) lanes of a warp owns one
-// texel and its R rays (R / G rays per lane), so 32 / G texels share a warp.
-// Each lane
-//   * draws its directions from Philox-4x32-10 (Salmon et al., SC'11) with
+// Each masked coarse voxel contributes its 8 fine children ("texel slots");
+// each slot casts R rays, so the frame's work is a flat list of
+// 8 * masked * R ray ids (consecutive ids share a texel).  Per ray:
+//   * the direction comes from Philox-4x32-10 (Salmon et al., SC'11) with
 //     counter (draw, ray, frame, texel) and key (seed lo, seed hi), mapped to
 //     the sphere by Marsaglia's (1972) rejection method -- integer accept
 //     test, fp32 map, so every direction is bit-reproducible;
-//   * finds the closest hit by a stack traversal of the binary BVH (both
-//     child boxes per node fetch, nearer child first, the farther one pushed
-//     with its entry distance and skipped on pop when it can no longer hold
-//     a closer hit), testing leaves with Moller-Trumbore in fp32 with the
-//     operation order written out (explicit fma / rounding intrinsics);
-//     equal distances keep the smaller original triangle index.
-// The group then reduces (min distance, #front, #back) with shuffles and its
-// first lane applies u_t = min(u, r_t) (Eq. 1; the alpha decay was applied by
-// the mask kernel), adds the counts and writes f_t = +-u_t (c_t while no ray
-// has hit), negative when back hits outnumber front hits.
+//   * the closest hit comes from a stack traversal of the 4-wide BVH (one
+//     128-byte node fetch tests four child boxes; the nearest hit child is
+//     entered next, the others pushed farthest-first with their entry
+//     distance and skipped on pop once they cannot hold a closer hit),
+//     leaves tested with Moller-Trumbore in fp32 with the operation
+//     order written out (explicit fma / rounding intrinsics); equal
+//     distances keep the smaller original triangle index.
+// Rays of very different lengths would leave most lanes of a lock-step warp
+// idle, so warps are persistent and refill idle lanes with new ray ids from
+// a warp-local chunk.  A finished ray commits its distance (atomicMin on the
+// float bits, t >= 0) and its front/back hit into per-slot scratch with
+// warp-aggregated atomics; k_trace_finalize then applies Eq. 1 per texel:
+// u_t = min(u, r_t) (the alpha decay was applied by the mask kernel), the
+// counts, and f_t = +-u_t (c_t while no ray has hit), negative when back
+// hits outnumber front hits.
 #include <math_constants.h>
 
 #include "internal.cuh"
@@ -30,10 +34,10 @@ struct TraceArgs {
     const uint32_t* masked;
     const uint32_t* count;
     int nc;
-    int rays, log2_group, rays_per_lane;
+    int rays, log2_rays;
     uint32_t key0, key1, frame;
     float bx, by, bz, hf;
-    const BNode* nodes;
+    const WNode* wide;
     const float4* tri;
     long long nt;
     const float* coarse;
@@ -42,6 +46,9 @@ struct TraceArgs {
     float* fine;
     uint32_t* err;
     TraceCounters* counters;   // work counters (counting variant only)
+    uint32_t* ray_min;         // [8 nc^3] per texel slot: min hit distance bits of this frame
+    uint32_t* ray_cnt;         // [8 nc^3] per texel slot: front | back << 16 hits of this frame
+    unsigned long long* next_ray;
 };
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -118,161 +125,272 @@ __device__ __forceinline__ float safe_inv(float d) {
     return __fdiv_rn(1.0f, fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
 }
 
-struct Hit {
-    float t;
-    int idx;
-    bool front;
+// Per-lane ray state of the persistent tracer.
+struct Ray {
+    float3 o, d, id, oid;
+    float bt;          // closest hit distance so far
+    int bidx;          // its original triangle index (0x7FFFFFFF: none)
+    bool bfront;
+    int node;          // next node to enter (>= 0 internal, < 0 ~leaf)
+    int sp;
+    uint32_t slot;     // texel slot = 8 * (masked-list position) + child
+    uint32_t steps;    // nodes entered; a tree of 2 nt - 1 nodes bounds it
+};
+
+__device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r) {
+    const uint32_t slot = (uint32_t)(g >> a.log2_rays);
+    const uint32_t ray = (uint32_t)(g & (uint64_t)(a.rays - 1));
+    const uint32_t parent = a.masked[slot >> 3];
+    const uint32_t ch = slot & 7u;
+    const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
+    const uint32_t px = parent % nc, py = (parent / nc) % nc, pz = parent / (nc * nc);
+    const uint32_t jx = 2 * px + (ch & 1), jy = 2 * py + ((ch >> 1) & 1), jz = 2 * pz + (ch >> 2);
+    const uint32_t texel = jx + nf * (jy + nf * jz);
+    r.o = make_float3(__fadd_rn(a.bx, __fmul_rn(__fadd_rn((float)jx, 0.5f), a.hf)),
+                      __fadd_rn(a.by, __fmul_rn(__fadd_rn((float)jy, 0.5f), a.hf)),
+                      __fadd_rn(a.bz, __fmul_rn(__fadd_rn((float)jz, 0.5f), a.hf)));
+    r.d = sphere_dir(a.key0, a.key1, texel, a.frame, ray);
+    r.id = make_float3(safe_inv(r.d.x), safe_inv(r.d.y), safe_inv(r.d.z));
+    r.oid = make_float3(r.o.x * r.id.x, r.o.y * r.id.y, r.o.z * r.id.z);
+    r.bt = CUDART_INF_F;
+    r.bidx = 0x7FFFFFFF;
+    r.bfront = false;
+    r.node = a.nt > 1 ? 0 : ~0;
+    r.sp = 0;
+    r.slot = slot;
+    r.steps = 0;
+}
+
+// One traversal step (enter one node or test one leaf).  Returns true when
+// the ray's traversal is complete.
+constexpr int TRACE_THREADS = 128;
+constexpr int SMEM_STACK = 24;
+
+struct Stack {
+    int* id;      // &s_id[0][thread], stride TRACE_THREADS
+    float* t;     // &s_t[0][thread]
+    int2* deep;   // local overflow
+    __device__ __forceinline__ void push(int sp, int node, float t0) {
+        if (sp < SMEM_STACK) {
+            id[sp * TRACE_THREADS] = node;
+            t[sp * TRACE_THREADS] = t0;
+        } else {
+            deep[sp - SMEM_STACK] = make_int2(node, __float_as_int(t0));
+        }
+    }
+    __device__ __forceinline__ void pop(int sp, int& node, float& t0) const {
+        if (sp < SMEM_STACK) {
+            node = id[sp * TRACE_THREADS];
+            t0 = t[sp * TRACE_THREADS];
+        } else {
+            const int2 e = deep[sp - SMEM_STACK];
+            node = e.x;
+            t0 = __int_as_float(e.y);
+        }
+    }
 };
 
 template <bool COUNT>
-__device__ __forceinline__ void closest_hit(const TraceArgs& a, float3 o, float3 d, Hit& h, uint32_t& visits_out,
-                                            uint32_t& tests_out) {
-    h.t = CUDART_INF_F;
-    h.idx = 0x7FFFFFFF;
-    h.front = false;
-    if (a.nt == 0) return;
-    const float3 id = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
-    const float3 oid = make_float3(o.x * id.x, o.y * id.y, o.z * id.z);
-    int2 stack[TRACE_STACK];
-    int sp = 0;
-    int node = a.nt > 1 ? 0 : ~0;
-    // every node is entered at most once per ray (2 nt - 1 nodes); the bound
-    // only guards against a damaged tree
-    for (long long visits = 0;; visits++) {
-        if (visits > 2 * a.nt) {
-            atomicOr(a.err, ERR_STACK);
-            return;
+__device__ __forceinline__ bool step_ray(const TraceArgs& a, Ray& r, Stack& stack, uint32_t& visits,
+                                         uint32_t& tests) {
+    if (COUNT) visits++;
+    if (++r.steps > 2u * (uint32_t)a.nt + 2u) {   // only a damaged tree gets here
+        atomicOr(a.err, ERR_STACK);
+        return true;
+    }
+    const int node = r.node;
+    if (node >= 0) {
+        // 4-wide node: test the four child boxes, visit the nearest hit child
+        // next and push the others farthest-first with their entry distance
+        const WNode* w = a.wide + node;
+        const float4 lx = __ldg(&w->lox), hx = __ldg(&w->hix);
+        const float4 ly = __ldg(&w->loy), hy = __ldg(&w->hiy);
+        const float4 lz = __ldg(&w->loz), hz = __ldg(&w->hiz);
+        const int4 ch = __ldg(&w->child);
+        float key[4];
+        int val[4] = {ch.x, ch.y, ch.z, ch.w};
+        const float blx[4] = {lx.x, lx.y, lx.z, lx.w}, bhx[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float bly[4] = {ly.x, ly.y, ly.z, ly.w}, bhy[4] = {hy.x, hy.y, hy.z, hy.w};
+        const float blz[4] = {lz.x, lz.y, lz.z, lz.w}, bhz[4] = {hz.x, hz.y, hz.z, hz.w};
+        int nh = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float x0 = fmaf(blx[k], r.id.x, -r.oid.x), x1 = fmaf(bhx[k], r.id.x, -r.oid.x);
+            const float y0 = fmaf(bly[k], r.id.y, -r.oid.y), y1 = fmaf(bhy[k], r.id.y, -r.oid.y);
+            const float z0 = fmaf(blz[k], r.id.z, -r.oid.z), z1 = fmaf(bhz[k], r.id.z, -r.oid.z);
+            const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.f));
+            const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), r.bt));
+            const bool hit = t0 <= t1 && val[k] != WIDE_EMPTY;
+            key[k] = hit ? t0 : CUDART_INF_F;
+            nh += hit;
         }
-        if (COUNT) visits_out++;
-        if (node >= 0) {
-            const float4 na = __ldg(&a.nodes[node].a);
-            const float4 nb = __ldg(&a.nodes[node].b);
-            const float4 nc = __ldg(&a.nodes[node].c);
-            const int4 nd = __ldg(&a.nodes[node].d);
-            // left child box: (na.x, na.y) x, (na.z, na.w) y, (nc.x, nc.y) z
-            float x0 = fmaf(na.x, id.x, -oid.x), x1 = fmaf(na.y, id.x, -oid.x);
-            float y0 = fmaf(na.z, id.y, -oid.y), y1 = fmaf(na.w, id.y, -oid.y);
-            float z0 = fmaf(nc.x, id.z, -oid.z), z1 = fmaf(nc.y, id.z, -oid.z);
-            const float tl0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.f));
-            const float tl1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), h.t));
-            x0 = fmaf(nb.x, id.x, -oid.x); x1 = fmaf(nb.y, id.x, -oid.x);
-            y0 = fmaf(nb.z, id.y, -oid.y); y1 = fmaf(nb.w, id.y, -oid.y);
-            z0 = fmaf(nc.z, id.z, -oid.z); z1 = fmaf(nc.w, id.z, -oid.z);
-            const float tr0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.f));
-            const float tr1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), h.t));
-            const bool hl = tl0 <= tl1, hr = tr0 <= tr1;
-            if (hl && hr) {
-                const bool lfirst = tl0 <= tr0;
-                const int far = lfirst ? nd.y : nd.x;
-                const float tfar = lfirst ? tr0 : tl0;
-                if (sp < TRACE_STACK) stack[sp++] = make_int2(far, __float_as_int(tfar));
-                else atomicOr(a.err, ERR_STACK);
-                node = lfirst ? nd.x : nd.y;
-                continue;
-            }
-            if (hl) { node = nd.x; continue; }
-            if (hr) { node = nd.y; continue; }
-        } else {
-            const int leaf = ~node;
-            if (COUNT) tests_out++;
-            const float4 p0 = __ldg(&a.tri[3 * leaf]);
-            const float4 p1 = __ldg(&a.tri[3 * leaf + 1]);
-            const float4 p2 = __ldg(&a.tri[3 * leaf + 2]);
-            float t;
-            bool fr;
-            if (ray_tri(o, d, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
-                        make_float3(p2.x, p2.y, p2.z), t, fr)) {
-                const int idx = __float_as_int(p0.w);
-                if (t < h.t || (t == h.t && idx < h.idx)) {
-                    h.t = t;
-                    h.idx = idx;
-                    h.front = fr;
+        if (nh > 0) {
+            // ascending sort of (key, val): a 5-exchange network
+#define RTSDF_CAS(i, j)                                                     \
+    if (key[j] < key[i]) {                                                  \
+        const float tk = key[i]; key[i] = key[j]; key[j] = tk;              \
+        const int tv = val[i]; val[i] = val[j]; val[j] = tv;                \
+    }
+            RTSDF_CAS(0, 1) RTSDF_CAS(2, 3) RTSDF_CAS(0, 2) RTSDF_CAS(1, 3) RTSDF_CAS(1, 2)
+#undef RTSDF_CAS
+#pragma unroll
+            for (int k = 3; k >= 1; k--) {
+                if (k < nh) {
+                    if (r.sp < TRACE_STACK) stack.push(r.sp++, val[k], key[k]);
+                    else atomicOr(a.err, ERR_STACK);
                 }
             }
+            r.node = val[0];
+            return false;
         }
-        // pop the next candidate that can still hold a hit at distance <= h.t
-        for (;;) {
-            if (sp == 0) return;
-            const int2 e = stack[--sp];
-            if (__int_as_float(e.y) <= h.t) {
-                node = e.x;
-                break;
+    } else {
+        if (COUNT) tests++;
+        const int leaf = ~node;
+        const float4 p0 = __ldg(&a.tri[3 * leaf]);
+        const float4 p1 = __ldg(&a.tri[3 * leaf + 1]);
+        const float4 p2 = __ldg(&a.tri[3 * leaf + 2]);
+        float t;
+        bool fr;
+        if (ray_tri(r.o, r.d, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                    make_float3(p2.x, p2.y, p2.z), t, fr)) {
+            const int idx = __float_as_int(p0.w);
+            if (t < r.bt || (t == r.bt && idx < r.bidx)) {
+                r.bt = t;
+                r.bidx = idx;
+                r.bfront = fr;
             }
         }
     }
+    // pop the next entry that can still hold a hit at distance <= bt
+    while (r.sp > 0) {
+        int nx;
+        float te;
+        stack.pop(--r.sp, nx, te);
+        if (te <= r.bt) {
+            r.node = nx;
+            return false;
+        }
+    }
+    return true;
 }
 
+constexpr int RAY_CHUNK = 256;   // rays a warp takes from the global counter at a time
+constexpr int REFILL_MIN = 4;    // refill once this many lanes are idle
+
+// Persistent warps: each lane traces one ray at a time and takes a new one
+// as soon as it finishes (from a warp-local chunk of consecutive ray ids, so
+// the lanes of a warp mostly share a texel and its origin).  Finished rays
+// commit (min distance, front/back) per texel slot with warp-aggregated
+// atomics; k_trace_finalize then applies Eq. 1 per texel.
 template <bool COUNT>
-__global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
-    uint32_t n_rays = 0, n_visits = 0, n_tests = 0;
-    const uint32_t n_vox = *a.count;
-    const uint64_t n_tex = (uint64_t)n_vox * 8u;
-    const int G = 1 << a.log2_group;              // lanes per texel
-    const int tpw = 32 >> a.log2_group;           // texels per warp
+__global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
+    uint32_t n_visits = 0, n_tests = 0, n_rays = 0;
+    const uint64_t total = (uint64_t)(*a.count) * 8u * (uint64_t)a.rays;
     const unsigned lane = threadIdx.x & 31;
-    const unsigned sub = lane & (G - 1);
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
-    const int nf = 2 * a.nc;
-    for (uint64_t base = warp * tpw; base < n_tex; base += nwarps * tpw) {
-        const uint64_t slot = base + (lane >> a.log2_group);
-        const bool valid = slot < n_tex;
-        float rmin = CUDART_INF_F;
-        uint32_t nfr = 0, nbk = 0;
-        uint32_t texel = 0;
-        uint32_t parent = 0;
-        if (valid) {
-            parent = a.masked[slot >> 3];
-            const uint32_t ch = (uint32_t)(slot & 7);
-            const uint32_t px = parent % a.nc, py = (parent / a.nc) % a.nc, pz = parent / (a.nc * a.nc);
-            const uint32_t jx = 2 * px + (ch & 1), jy = 2 * py + ((ch >> 1) & 1), jz = 2 * pz + (ch >> 2);
-            texel = jx + nf * (jy + nf * jz);
-            const float3 o = make_float3(__fadd_rn(a.bx, __fmul_rn(__fadd_rn((float)jx, 0.5f), a.hf)),
-                                         __fadd_rn(a.by, __fmul_rn(__fadd_rn((float)jy, 0.5f), a.hf)),
-                                         __fadd_rn(a.bz, __fmul_rn(__fadd_rn((float)jz, 0.5f), a.hf)));
-            for (int k = 0; k < a.rays_per_lane; k++) {
-                const uint32_t ray = sub + (uint32_t)k * G;
-                const float3 d = sphere_dir(a.key0, a.key1, texel, a.frame, ray);
-                Hit h;
-                closest_hit<COUNT>(a, o, d, h, n_visits, n_tests);
-                if (COUNT) n_rays++;
-                if (h.idx != 0x7FFFFFFF) {
-                    rmin = fminf(rmin, h.t);
-                    if (h.front) nfr++;
-                    else nbk++;
+    const unsigned lt = (1u << lane) - 1u;
+    // traversal stack: the first SMEM_STACK entries in shared memory laid out
+    // [entry][thread] (each push or pop of a warp touches 32 distinct banks),
+    // deeper entries in local memory
+    __shared__ int s_id[SMEM_STACK][TRACE_THREADS];
+    __shared__ float s_t[SMEM_STACK][TRACE_THREADS];
+    int2 deep[TRACE_STACK - SMEM_STACK];
+    Stack stk{&s_id[0][threadIdx.x], &s_t[0][threadIdx.x], deep};
+    Ray r;
+    bool active = false;
+    uint64_t chunk_next = 0, chunk_end = 0;   // warp-uniform
+    bool exhausted = false;                    // warp-uniform
+    for (;;) {
+        // hand out rays to idle lanes
+        unsigned idle = __ballot_sync(0xFFFFFFFFu, !active);
+        while (idle && !exhausted) {
+            if (chunk_next == chunk_end) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(a.next_ray, (unsigned long long)RAY_CHUNK);
+                b = __shfl_sync(0xFFFFFFFFu, b, 0);
+                if (b >= total) {
+                    exhausted = true;
+                    break;
+                }
+                chunk_next = b;
+                chunk_end = min((uint64_t)b + RAY_CHUNK, total);
+            }
+            const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
+            const uint32_t want = __popc(idle);
+            const uint32_t take = min(avail, want);
+            if (!active) {
+                const uint32_t rank = __popc(idle & lt);
+                if (rank < take) {
+                    setup_ray(a, chunk_next + rank, r);
+                    active = true;
+                    if (COUNT) n_rays++;
                 }
             }
+            chunk_next += take;
+            idle = __ballot_sync(0xFFFFFFFFu, !active);
         }
-        // reduce over the G lanes of the texel group
-        for (int off = G >> 1; off >= 1; off >>= 1) {
-            rmin = fminf(rmin, __shfl_xor_sync(0xFFFFFFFFu, rmin, off));
-            nfr += __shfl_xor_sync(0xFFFFFFFFu, nfr, off);
-            nbk += __shfl_xor_sync(0xFFFFFFFFu, nbk, off);
-        }
-        if (valid && sub == 0) {
-            const float u = fminf(a.accum[texel], rmin);
-            const uint32_t cw = a.counts[texel];
-            const uint32_t f = min((cw & 0xFFFFu) + nfr, 0xFFFFu);
-            const uint32_t b = min((cw >> 16) + nbk, 0xFFFFu);
-            a.accum[texel] = u;
-            a.counts[texel] = f | (b << 16);
-            const float mag = u == CUDART_INF_F ? a.coarse[parent] : u;
-            a.fine[texel] = b > f ? -mag : mag;
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+        // trace until enough lanes are idle to be worth a refill
+        for (;;) {
+            bool done = false;
+            if (active) done = step_ray<COUNT>(a, r, stk, n_visits, n_tests);
+            const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
+            if (fin && done) {
+                const unsigned peers = __match_any_sync(fin, r.slot);
+                const bool hit = r.bidx != 0x7FFFFFFF;
+                const uint32_t tb = hit ? (__float_as_uint(r.bt) & 0x7FFFFFFFu) : 0x7F800000u;
+                const uint32_t cv = hit ? (r.bfront ? 1u : 0x10000u) : 0u;
+                const uint32_t mn = __reduce_min_sync(peers, tb);
+                const uint32_t sum = __reduce_add_sync(peers, cv);
+                if ((peers & lt) == 0) {
+                    if (mn != 0x7F800000u) atomicMin(a.ray_min + r.slot, mn);
+                    if (sum) atomicAdd(a.ray_cnt + r.slot, sum);
+                }
+                active = false;
+            }
+            const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
+            if (act == 0) break;
+            if (!exhausted && (32 - __popc(act)) >= REFILL_MIN) break;
         }
     }
     if (COUNT) {
-        unsigned long long r = n_rays, v = n_visits, t = n_tests;
+        unsigned long long rr = n_rays, v = n_visits, t = n_tests;
         for (int off = 16; off >= 1; off >>= 1) {
-            r += __shfl_xor_sync(0xFFFFFFFFu, r, off);
+            rr += __shfl_xor_sync(0xFFFFFFFFu, rr, off);
             v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
             t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&a.counters->rays, r);
+        if (lane == 0) {
+            atomicAdd(&a.counters->rays, rr);
             atomicAdd(&a.counters->visits, v);
             atomicAdd(&a.counters->tests, t);
         }
     }
+}
+
+// Eq. 1 per traced texel: u_t = min(u, r_t) (the alpha decay was applied by
+// the mask kernel), counts += this frame's front/back hits (saturating at
+// 16 bits), f_t = +-u_t or the coarse value while no ray has hit; the
+// per-slot scratch is cleared for the next frame.
+__global__ void k_trace_finalize(TraceArgs a) {
+    const uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (s >= (uint64_t)(*a.count) * 8u) return;
+    const uint32_t parent = a.masked[s >> 3];
+    const uint32_t ch = (uint32_t)(s & 7);
+    const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
+    const uint32_t px = parent % nc, py = (parent / nc) % nc, pz = parent / (nc * nc);
+    const uint32_t texel = (2 * px + (ch & 1)) + nf * ((2 * py + ((ch >> 1) & 1)) + nf * (2 * pz + (ch >> 2)));
+    const float rmin = __uint_as_float(a.ray_min[s]);
+    const uint32_t cv = a.ray_cnt[s];
+    a.ray_min[s] = 0x7F800000u;
+    a.ray_cnt[s] = 0u;
+    const float u = fminf(a.accum[texel], rmin);
+    const uint32_t cw = a.counts[texel];
+    const uint32_t f = min((cw & 0xFFFFu) + (cv & 0xFFFFu), 0xFFFFu);
+    const uint32_t b = min((cw >> 16) + (cv >> 16), 0xFFFFu);
+    a.accum[texel] = u;
+    a.counts[texel] = f | (b << 16);
+    const float mag = u == CUDART_INF_F ? a.coarse[parent] : u;
+    a.fine[texel] = b > f ? -mag : mag;
 }
 
 }  // namespace
@@ -285,8 +403,7 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.rays = rays;
     int lg = 0;
     while ((1 << lg) < rays) lg++;
-    a.log2_group = lg < 5 ? lg : 5;
-    a.rays_per_lane = rays >> a.log2_group;
+    a.log2_rays = lg;
     a.key0 = (uint32_t)c->cfg.seed;
     a.key1 = (uint32_t)(c->cfg.seed >> 32);
     a.frame = (uint32_t)frame;
@@ -294,7 +411,7 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.by = c->cfg.bmin[1];
     a.bz = c->cfg.bmin[2];
     a.hf = c->hf;
-    a.nodes = c->bvh.nodes;
+    a.wide = c->bvh.wide;
     a.tri = c->bvh.tri;
     a.nt = c->bvh.nt;
     a.coarse = c->coarse;
@@ -303,11 +420,21 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.fine = c->fine;
     a.err = c->d_err;
     a.counters = c->d_counters;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const unsigned grid = (unsigned)(sms > 0 ? sms : 132) * 16u;
-    if (c->counting) RTSDF_LAUNCH(c, k_trace<true>, grid, 128, 0, a);
-    else RTSDF_LAUNCH(c, k_trace<false>, grid, 128, 0, a);
+    a.ray_min = c->ray_min;
+    a.ray_cnt = c->ray_cnt;
+    a.next_ray = c->d_next_ray;
+    cudaError_t e = cudaMemsetAsync(c->d_next_ray, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    if (c->trace_grid == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, TRACE_THREADS, 0);
+        c->trace_grid = (unsigned)(sms > 0 ? sms : 132) * (unsigned)(per_sm > 0 ? per_sm : 4);
+    }
+    if (c->counting) RTSDF_LAUNCH(c, k_trace<true>, c->trace_grid, TRACE_THREADS, 0, a);
+    else RTSDF_LAUNCH(c, k_trace<false>, c->trace_grid, TRACE_THREADS, 0, a);
+    // one thread per possible slot; threads beyond the device count return
+    RTSDF_LAUNCH(c, k_trace_finalize, (unsigned)((8 * c->nc3 + 255) / 256), 256, 0, a);
     return cudaGetLastError();
 }
 
