@@ -203,6 +203,53 @@ rtsdf_status rtsdf_shadow_backward(rtsdf_t ctx, const float* sdf, const float* p
 rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* seeds_out, float* coarse_out,
                                int32_t n, float extent, float beta_vox, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent scenes (each its own context: grid size,
+ * mesh, BVH) updated together.  rtsdf_batch_frame runs the whole per-frame
+ * pipeline of Sec. 2.1-2.2 (voxelize, jump flood, mask, trace, Eq. 1) for
+ * every scene in one persistent cooperative kernel launch, replayed from a
+ * CUDA graph; each scene's result equals a plain per-scene frame (same
+ * kernels' arithmetic, same rays).  Scenes must be static within the batch
+ * (no pending rtsdf_move_objects).
+ * ------------------------------------------------------------------------ */
+typedef struct rtsdf_batch* rtsdf_batch_t;
+
+typedef struct {
+    int32_t blocks_per_sm;  /* persistent blocks per SM (0 = occupancy maximum) */
+    int32_t refill_min;     /* tracer: refill a warp once this many lanes are idle (1..32) */
+    int32_t ray_chunk;      /* tracer: rays a warp takes from the global counter at a time */
+    int32_t use_graph;      /* replay the frame from a CUDA graph (1) or launch directly (0) */
+    int32_t barrier_spins;  /* polls before a grid-barrier wait gives up with RTSDF_E_TIMEOUT
+                               (0 = default, about ten seconds) */
+} rtsdf_batch_tuning;
+
+typedef struct {
+    int32_t n_scenes;
+    int32_t grid;           /* blocks of the persistent launch */
+    int32_t graph;          /* 1 when frames replay a captured graph */
+    int64_t frames, launches;
+    float last_frame_ms;    /* device time of the last frame (CUDA events) */
+} rtsdf_batch_info;
+
+/* Creates n scene contexts (1 <= n <= 256) with the given configs.  All
+ * scenes share cfgs[0].stream; when it is NULL the batch creates its own
+ * non-blocking stream (graph capture cannot use the legacy default stream).
+ * Meshes are uploaded and BVHs built per scene through the plain API on the
+ * contexts returned by rtsdf_batch_context. */
+rtsdf_status rtsdf_batch_create(const rtsdf_config* cfgs, int32_t n, rtsdf_batch_t* out);
+rtsdf_status rtsdf_batch_destroy(rtsdf_batch_t batch);
+/* Borrowed context of scene i (owned by the batch). */
+rtsdf_status rtsdf_batch_context(rtsdf_batch_t batch, int32_t i, rtsdf_t* out);
+/* One frame for all scenes (arguments as rtsdf_trace).  Returns
+ * RTSDF_E_STATE when a scene lacks a mesh or a current BVH. */
+rtsdf_status rtsdf_batch_frame(rtsdf_batch_t batch, float d_vox, int32_t rays_per_texel, int32_t frame);
+/* Waits for the batch stream; returns RTSDF_E_TIMEOUT when a bounded
+ * grid-barrier wait expired, else the first device error of any scene. */
+rtsdf_status rtsdf_batch_sync(rtsdf_batch_t batch);
+rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_t batch, const rtsdf_batch_tuning* t);
+rtsdf_status rtsdf_batch_get_tuning(rtsdf_batch_t batch, rtsdf_batch_tuning* t);
+rtsdf_status rtsdf_batch_stats(rtsdf_batch_t batch, rtsdf_batch_info* out);
+
 /* Borrowed device views of the grids (no synchronisation). */
 rtsdf_status rtsdf_get_grids(rtsdf_t ctx, rtsdf_grids* out);
 

@@ -12,9 +12,9 @@ kernels behind the C ABI of ``include/rtsdf.h`` (``librtsdf.so``):
 The library must be built (``build.build()``); there is no CPU fallback.
 """
 from ._abi import RtsdfError, STATUS_NAMES  # noqa: F401
-from .context import RTSDF  # noqa: F401
+from .context import RTSDF, RTSDFBatch  # noqa: F401
 
-__all__ = ["RTSDF", "RtsdfError", "soft_shadow", "ShadowFn"]
+__all__ = ["RTSDF", "RTSDFBatch", "RtsdfError", "soft_shadow", "ShadowFn"]
 
 
 def __getattr__(name):

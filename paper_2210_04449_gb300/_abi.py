@@ -38,6 +38,16 @@ class Stats(ctypes.Structure):
                 ("node_visits", c_i64), ("tri_tests", c_i64)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", c_i32), ("refill_min", c_i32), ("ray_chunk", c_i32), ("use_graph", c_i32),
+                ("barrier_spins", c_i32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_scenes", c_i32), ("grid", c_i32), ("graph", c_i32), ("frames", c_i64), ("launches", c_i64),
+                ("last_frame_ms", c_f)]
+
+
 F3 = c_f * 3
 ctx_t = c_vp
 
@@ -57,6 +67,14 @@ SIGNATURES = {
     "rtsdf_shadow_backward": (status_t, [ctx_t, c_vp, c_vp, c_vp, c_i64, F3, c_f, c_i32, c_f, c_f, c_vp, c_vp,
                                          c_vp]),
     "rtsdf_jfa_noalloc": (status_t, [c_vp, c_vp, c_vp, c_i32, c_f, c_f, c_vp]),
+    "rtsdf_batch_create": (status_t, [ctypes.POINTER(Config), c_i32, ctypes.POINTER(c_vp)]),
+    "rtsdf_batch_destroy": (status_t, [c_vp]),
+    "rtsdf_batch_context": (status_t, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
+    "rtsdf_batch_frame": (status_t, [c_vp, c_f, c_i32, c_i32]),
+    "rtsdf_batch_sync": (status_t, [c_vp]),
+    "rtsdf_batch_set_tuning": (status_t, [c_vp, ctypes.POINTER(BatchTuning)]),
+    "rtsdf_batch_get_tuning": (status_t, [c_vp, ctypes.POINTER(BatchTuning)]),
+    "rtsdf_batch_stats": (status_t, [c_vp, ctypes.POINTER(BatchInfo)]),
     "rtsdf_get_grids": (status_t, [ctx_t, ctypes.POINTER(Grids)]),
     "rtsdf_get_masked_count": (status_t, [ctx_t, ctypes.POINTER(c_i64)]),
     "rtsdf_get_stats": (status_t, [ctx_t, ctypes.POINTER(Stats)]),

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librtsdf.so")
-SOURCES = ["api.cu", "voxelize.cu", "jfa.cu", "mask.cu", "bvh.cu", "trace.cu", "shadow.cu"]
+SOURCES = ["api.cu", "voxelize.cu", "jfa.cu", "mask.cu", "bvh.cu", "trace.cu", "shadow.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,8 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "rtsdf.h"), __file__]
+    deps = [src, os.path.join(INCLUDE, "rtsdf.h"), __file__] + [
+        os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -38,6 +38,18 @@ def _host_or_device(a, dtype):
     return arr.ctypes.data, 0, arr
 
 
+def make_config(coarse_n, bmin=(0.0, 0.0, 0.0), extent=1.0, beta_vox=0.5, alpha=1.0, seed=0, stream=0):
+    cfg = _abi.Config()
+    cfg.bmin = (ctypes.c_float * 3)(*[float(b) for b in bmin])
+    cfg.extent = float(extent)
+    cfg.coarse_n = int(coarse_n)
+    cfg.beta_vox = float(beta_vox)
+    cfg.alpha = float(alpha)
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.stream = stream
+    return cfg
+
+
 class RTSDF:
     """One SDF generator context (coarse grid N^3, fine grid (2N)^3) on one GPU.
 
@@ -47,23 +59,20 @@ class RTSDF:
     """
 
     def __init__(self, coarse_n: int, bmin=(0.0, 0.0, 0.0), extent: float = 1.0, beta_vox: float = 0.5,
-                 alpha: float = 1.0, seed: int = 0, stream=None, device=None):
+                 alpha: float = 1.0, seed: int = 0, stream=None, device=None, _borrowed=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("RTSDF needs a CUDA device (sm_103a); there is no CPU path")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._owned = _borrowed is None
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            cfg = _abi.Config()
-            cfg.bmin = (ctypes.c_float * 3)(*[float(b) for b in bmin])
-            cfg.extent = float(extent)
-            cfg.coarse_n = int(coarse_n)
-            cfg.beta_vox = float(beta_vox)
-            cfg.alpha = float(alpha)
-            cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
-            cfg.stream = self.stream.cuda_stream
-            h = ctypes.c_void_p()
-            call("rtsdf_create", ctypes.byref(cfg), ctypes.byref(h))
+            if _borrowed is not None:
+                h = _borrowed
+            else:
+                cfg = make_config(coarse_n, bmin, extent, beta_vox, alpha, seed, self.stream.cuda_stream)
+                h = ctypes.c_void_p()
+                call("rtsdf_create", ctypes.byref(cfg), ctypes.byref(h))
         self._h = h
         self.coarse_n = int(coarse_n)
         self.fine_n = 2 * int(coarse_n)
@@ -74,7 +83,8 @@ class RTSDF:
     # ------------------------------------------------------------ lifecycle
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
-            _abi.lib().rtsdf_destroy(self._h)
+            if self._owned:
+                _abi.lib().rtsdf_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
@@ -221,3 +231,65 @@ class RTSDF:
 
     def sync(self) -> None:
         call("rtsdf_sync", self._h)
+
+
+class RTSDFBatch:
+    """Many independent scenes updated by one persistent launch per frame
+    (``rtsdf_batch_*``).  ``scenes`` is a list of dicts with the RTSDF
+    constructor's keyword arguments (coarse_n, bmin, extent, beta_vox,
+    alpha, seed)."""
+
+    def __init__(self, scenes, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("RTSDFBatch needs a CUDA device (sm_103a); there is no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        n = len(scenes)
+        arr = (_abi.Config * n)()
+        sptr = 0 if stream is None else stream.cuda_stream
+        for i, sc in enumerate(scenes):
+            arr[i] = make_config(stream=sptr, **sc)
+        h = ctypes.c_void_p()
+        call("rtsdf_batch_create", arr, n, ctypes.byref(h))
+        self._h = h
+        self.scenes = []
+        for i, sc in enumerate(scenes):
+            ch = ctypes.c_void_p()
+            call("rtsdf_batch_context", h, i, ctypes.byref(ch))
+            kw = dict(sc)
+            self.scenes.append(RTSDF(_borrowed=ch, **kw))
+
+    def frame(self, d_vox: float, rays_per_texel: int, frame: int) -> None:
+        call("rtsdf_batch_frame", self._h, float(d_vox), int(rays_per_texel), int(frame))
+
+    def sync(self) -> None:
+        call("rtsdf_batch_sync", self._h)
+
+    def get_tuning(self) -> dict:
+        t = _abi.BatchTuning()
+        call("rtsdf_batch_get_tuning", self._h, ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in _abi.BatchTuning._fields_}
+
+    def set_tuning(self, **kw) -> None:
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = _abi.BatchTuning(**cur)
+        call("rtsdf_batch_set_tuning", self._h, ctypes.byref(t))
+
+    def stats(self) -> dict:
+        s = _abi.BatchInfo()
+        call("rtsdf_batch_stats", self._h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in _abi.BatchInfo._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            for sc in self.scenes:
+                sc._h = ctypes.c_void_p()
+            _abi.lib().rtsdf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

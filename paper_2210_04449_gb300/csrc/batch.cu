@@ -1,0 +1,743 @@
+// Batched form: many independent scenes of uneven grid and mesh size, the
+// whole per-frame pipeline (clear, voxelize, jump flood, mask, trace, Eq. 1
+// finalize) for all of them in ONE persistent cooperative launch, replayed
+// from a CUDA graph.
+//
+// Work of every stage is flattened over the scenes through prefix sums (a
+// thread finds its scene by binary search), so small scenes do not leave
+// the GPU idle and no per-scene launch or tail is paid.  Stages are separated
+// by a grid-wide barrier; the tracer fetches rays dynamically across all
+// scenes.  The arithmetic is the per-scene path's own (vox_dev.cuh,
+// jfa_dev.cuh, trace_dev.cuh), so each scene's result equals a plain
+// per-scene frame bit for bit.
+//
+// The barrier is an arrival counter plus a generation word.  Its waits are
+// bounded: after BARRIER_SPINS polls a block records ERR_TIMEOUT, raises a
+// shared abort flag and the whole kernel returns (rtsdf_batch_sync then
+// reports RTSDF_E_TIMEOUT); the cooperative launch guarantees that all
+// blocks are resident, so the bound only guards against a broken launch.
+#include <math.h>
+#include <math_constants.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "jfa_dev.cuh"
+#include "trace_dev.cuh"
+#include "vox_dev.cuh"
+
+namespace rtsdf {
+namespace {
+
+using namespace dev;
+
+constexpr int MAX_BATCH = 256;
+constexpr uint32_t BARRIER_SPINS = 1u << 27;   // default polls (>= 64 ns each): several seconds
+
+struct SceneDesc {
+    TraceArgs t;              // tracer fields (rays / frame filled in per frame)
+    const int32_t* q;         // quantised vertices
+    const int32_t* tris;
+    long long n_tris;
+    uint32_t* seeds[2];
+    float hc, beta_h, beta_vox, alpha;
+    int passes;
+};
+
+struct BatchParams {
+    uint32_t frame;
+    int rays, log2_rays;
+    float d_vox;
+};
+
+struct BvhRef {
+    const WNode* wide;
+    const float4* tri;
+    long long nt;
+    uint32_t* err;
+};
+
+struct BatchArgs {
+    const SceneDesc* sc;
+    int ns;
+    const BatchParams* params;
+    const unsigned long long* vox_prefix;   // [ns + 1] coarse voxels
+    const unsigned long long* tri_prefix;   // [ns + 1] triangles
+    int max_passes;
+    int2* big_list;                         // (scene, triangle) of large triangles
+    uint32_t* big_count;
+    unsigned long long* next_ray;
+    uint32_t* bar_count;
+    uint32_t* bar_gen;
+    uint32_t* abort;
+    uint32_t* err;
+    int refill_min;
+    int ray_chunk;
+    uint32_t spins;
+};
+
+__device__ __forceinline__ int find_scene(const unsigned long long* prefix, int ns, unsigned long long g) {
+    int lo = 0, hi = ns - 1;   // largest s with prefix[s] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ bool grid_barrier(const BatchArgs& b) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* gen = b.bar_gen;
+        volatile uint32_t* abort = b.abort;
+        const uint32_t g0 = *gen;
+        __threadfence();
+        if (atomicAdd(b.bar_count, 1u) + 1u == gridDim.x) {
+            *b.bar_count = 0u;
+            __threadfence();
+            atomicAdd(b.bar_gen, 1u);
+        } else {
+            for (uint32_t it = 0; *gen == g0 && *abort == 0u; it++) {
+                if (it > b.spins) {
+                    atomicOr(b.err, ERR_TIMEOUT);
+                    atomicExch(b.abort, 1u);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = *abort == 0u;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS, 6) k_batch_frame(BatchArgs b) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nthr = gridDim.x * (uint64_t)blockDim.x;
+    const BatchParams P = *b.params;
+    const int ns = b.ns;
+    const unsigned long long total_vox = b.vox_prefix[ns], total_tris = b.tri_prefix[ns];
+
+    // ---- stage 0: clear the seed grids and the per-scene counters
+    for (uint64_t g = tid; g < total_vox; g += nthr) {
+        const int s = find_scene(b.vox_prefix, ns, g);
+        b.sc[s].seeds[0][g - b.vox_prefix[s]] = SEED_EMPTY;
+    }
+    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) *const_cast<uint32_t*>(b.sc[s].t.count) = 0u;
+    if (tid == 0) {
+        *b.big_count = 0u;
+        *b.next_ray = 0ull;
+    }
+    if (!grid_barrier(b)) return;
+
+    // ---- stage 1: voxelize (small triangles inline, large ones listed)
+    for (uint64_t g = tid; g < total_tris; g += nthr) {
+        const int s = find_scene(b.tri_prefix, ns, g);
+        const SceneDesc& d = b.sc[s];
+        const long long t = (long long)(g - b.tri_prefix[s]);
+        const int n = d.t.nc;
+        TriAxes ax;
+        setup(d.q, d.tris, t, n, ax);
+        const int cx = ax.hi[0] - ax.lo[0] + 1, cy = ax.hi[1] - ax.lo[1] + 1, cz = ax.hi[2] - ax.lo[2] + 1;
+        if (cx <= 0 || cy <= 0 || cz <= 0) continue;
+        if ((long long)cx * cy * cz > SMALL_MAX) {
+            b.big_list[atomicAdd(b.big_count, 1u)] = make_int2(s, (int)t);
+            continue;
+        }
+        for (int z = ax.lo[2]; z <= ax.hi[2]; z++)
+            for (int y = ax.lo[1]; y <= ax.hi[1]; y++)
+                for (int x = ax.lo[0]; x <= ax.hi[0]; x++)
+                    if (overlaps(ax, x, y, z)) d.seeds[0][x + (size_t)n * (y + (size_t)n * z)] = pack_seed(x, y, z);
+    }
+    if (!grid_barrier(b)) return;
+
+    // ---- stage 2: large triangles, one block each
+    {
+        const uint32_t nb = *(volatile uint32_t*)b.big_count;
+        for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+            const int2 it = b.big_list[i];
+            const SceneDesc& d = b.sc[it.x];
+            const int n = d.t.nc;
+            TriAxes ax;
+            setup(d.q, d.tris, it.y, n, ax);
+            const int cx = ax.hi[0] - ax.lo[0] + 1, cy = ax.hi[1] - ax.lo[1] + 1, cz = ax.hi[2] - ax.lo[2] + 1;
+            const long long tot = (long long)cx * cy * cz;
+            for (long long v = threadIdx.x; v < tot; v += blockDim.x) {
+                const int x = ax.lo[0] + (int)(v % cx), y = ax.lo[1] + (int)((v / cx) % cy);
+                const int z = ax.lo[2] + (int)(v / ((long long)cx * cy));
+                if (overlaps(ax, x, y, z)) d.seeds[0][x + (size_t)n * (y + (size_t)n * z)] = pack_seed(x, y, z);
+            }
+        }
+    }
+    if (!grid_barrier(b)) return;
+
+    // ---- stage 3: jump flooding, pass p of every scene that has one
+    for (int p = 0; p < b.max_passes; p++) {
+        for (uint64_t g = tid; g < total_vox; g += nthr) {
+            const int s = find_scene(b.vox_prefix, ns, g);
+            const SceneDesc& d = b.sc[s];
+            const int L = d.passes;
+            if (p >= L) continue;
+            const int n = d.t.nc;
+            const uint64_t v = g - b.vox_prefix[s];
+            const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((uint64_t)n * n));
+            const uint32_t* in = d.seeds[p & 1];
+            uint32_t* out = d.seeds[(p + 1) & 1];
+            float* coarse = const_cast<float*>(d.t.coarse);
+            if (p == L - 1) jfa_voxel<true, false>(in, out, n, 1 << (L - 1 - p), x, y, z, coarse, d.hc, d.beta_h);
+            else jfa_voxel<false, false>(in, out, n, 1 << (L - 1 - p), x, y, z, coarse, d.hc, d.beta_h);
+        }
+        if (!grid_barrier(b)) return;
+    }
+    // scenes without jump steps (N = 1): coarse value straight from the seed
+    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) {
+        const SceneDesc& d = b.sc[s];
+        if (d.passes == 0) {
+            const uint32_t sv = d.seeds[0][0];
+            const_cast<float*>(d.t.coarse)[0] = coarse_value(sv, seed_d2(sv, 0u, 0u), d.hc, d.beta_h);
+        }
+    }
+    if (!grid_barrier(b)) return;
+
+    // ---- stage 4: near-surface mask, fill, Eq. 1 decay (static scenes: no reset)
+    {
+        const unsigned lane = threadIdx.x & 31;
+        const uint64_t warp0 = tid - lane;
+        for (uint64_t base = warp0; base < total_vox; base += nthr) {
+            const uint64_t g = base + lane;
+            const bool valid = g < total_vox;
+            int s = 0;
+            bool masked = false;
+            uint64_t v = 0;
+            if (valid) {
+                s = find_scene(b.vox_prefix, ns, g);
+                const SceneDesc& d = b.sc[s];
+                const int n = d.t.nc;
+                v = g - b.vox_prefix[s];
+                const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((uint64_t)n * n));
+                const uint32_t sv = d.seeds[d.passes & 1][v];
+                const double sd = (double)P.d_vox + (double)d.beta_vox;
+                const long long T = sd < 0 ? -1 : (long long)floor(sd * sd);
+                if (sv != SEED_EMPTY) {
+                    const int dx = (int)(sv & 0xFF) - x, dy = (int)((sv >> 8) & 0xFF) - y, dz = (int)((sv >> 16) & 0xFF) - z;
+                    masked = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz <= T;
+                }
+                const float c = d.t.coarse[v];
+                const int nf = 2 * n;
+                for (int cz = 0; cz < 2; cz++)
+                    for (int cy = 0; cy < 2; cy++)
+                        for (int cxx = 0; cxx < 2; cxx++) {
+                            const size_t j = (size_t)(2 * x + cxx) + (size_t)nf * ((size_t)(2 * y + cy) + (size_t)nf * (2 * z + cz));
+                            const float u = d.t.accum[j];
+                            if (!masked) {
+                                d.t.fine[j] = c;
+                                if (u != CUDART_INF_F) {
+                                    d.t.accum[j] = CUDART_INF_F;
+                                    d.t.counts[j] = 0u;
+                                }
+                            } else if (d.alpha != 1.f) {
+                                float un = u;
+                                if (d.alpha == 0.f) un = c;
+                                else if (u != CUDART_INF_F)
+                                    un = __fadd_rn(__fmul_rn(d.alpha, u), __fmul_rn(1.f - d.alpha, c));
+                                if (un != u) d.t.accum[j] = un;
+                            }
+                        }
+            }
+            // warp-aggregated append per scene
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, masked);
+            if (masked) {
+                const unsigned peers = __match_any_sync(bal, s);
+                const int leader = __ffs(peers) - 1;
+                uint32_t base_slot = 0;
+                if ((int)lane == leader)
+                    base_slot = atomicAdd(const_cast<uint32_t*>(b.sc[s].t.count), (uint32_t)__popc(peers));
+                base_slot = __shfl_sync(peers, base_slot, leader);
+                const_cast<uint32_t*>(b.sc[s].t.masked)[base_slot + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)v;
+            }
+        }
+    }
+    if (!grid_barrier(b)) return;
+
+    // ---- stage 5: trace all scenes' rays with dynamic fetch
+    __shared__ unsigned long long s_rp[MAX_BATCH + 1];   // ray prefix over scenes
+    __shared__ int s_id[SMEM_STACK][TRACE_THREADS];
+    __shared__ float s_t[SMEM_STACK][TRACE_THREADS];
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int s = 0; s < ns; s++) {
+            s_rp[s] = acc;
+            acc += (unsigned long long)(*(volatile const uint32_t*)b.sc[s].t.count) * 8ull * (unsigned long long)P.rays;
+        }
+        s_rp[ns] = acc;
+    }
+    __syncthreads();
+    {
+        const unsigned long long total = s_rp[ns];
+        const unsigned lane = threadIdx.x & 31;
+        const unsigned lt = (1u << lane) - 1u;
+        int2 deep[TRACE_STACK - SMEM_STACK];
+        Stack stk{&s_id[0][threadIdx.x], &s_t[0][threadIdx.x], deep};
+        Ray r;
+        BvhRef bv{nullptr, nullptr, 0, b.err};
+        int scene = 0;
+        bool active = false;
+        unsigned long long chunk_next = 0, chunk_end = 0;
+        bool exhausted = false;
+        uint32_t dummy_v = 0, dummy_t = 0;
+        for (;;) {
+            unsigned idle = __ballot_sync(0xFFFFFFFFu, !active);
+            while (idle && !exhausted) {
+                if (chunk_next == chunk_end) {
+                    unsigned long long c0 = 0;
+                    if (lane == 0) c0 = atomicAdd(b.next_ray, (unsigned long long)b.ray_chunk);
+                    c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+                    if (c0 >= total) {
+                        exhausted = true;
+                        break;
+                    }
+                    chunk_next = c0;
+                    chunk_end = min(c0 + (unsigned long long)b.ray_chunk, total);
+                }
+                const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
+                const uint32_t want = __popc(idle);
+                const uint32_t take = min(avail, want);
+                if (!active) {
+                    const uint32_t rank = __popc(idle & lt);
+                    if (rank < take) {
+                        const unsigned long long g = chunk_next + rank;
+                        scene = find_scene(s_rp, ns, g);
+                        TraceArgs ta = b.sc[scene].t;
+                        ta.rays = P.rays;
+                        ta.log2_rays = P.log2_rays;
+                        ta.frame = P.frame;
+                        setup_ray(ta, g - s_rp[scene], r);
+                        bv.wide = ta.wide;
+                        bv.tri = ta.tri;
+                        bv.nt = ta.nt;
+                        active = true;
+                    }
+                }
+                chunk_next += take;
+                idle = __ballot_sync(0xFFFFFFFFu, !active);
+            }
+            if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+            for (;;) {
+                bool done = false;
+                if (active) done = step_ray<false>(bv, r, stk, dummy_v, dummy_t);
+                const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
+                if (fin && done) {
+                    const unsigned long long key = ((unsigned long long)scene << 32) | r.slot;
+                    const unsigned peers = __match_any_sync(fin, key);
+                    const bool hit = r.bidx != 0x7FFFFFFF;
+                    const uint32_t tb = hit ? (__float_as_uint(r.bt) & 0x7FFFFFFFu) : 0x7F800000u;
+                    const uint32_t cv = hit ? (r.bfront ? 1u : 0x10000u) : 0u;
+                    const uint32_t mn = __reduce_min_sync(peers, tb);
+                    const uint32_t sum = __reduce_add_sync(peers, cv);
+                    if ((peers & lt) == 0) {
+                        if (mn != 0x7F800000u) atomicMin(b.sc[scene].t.ray_min + r.slot, mn);
+                        if (sum) atomicAdd(b.sc[scene].t.ray_cnt + r.slot, sum);
+                    }
+                    active = false;
+                }
+                const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
+                if (act == 0) break;
+                if (!exhausted && (32 - __popc(act)) >= b.refill_min) break;
+            }
+        }
+    }
+    if (!grid_barrier(b)) return;
+
+    // ---- stage 6: Eq. 1 finalize of every traced texel slot
+    {
+        unsigned long long total_slots = 0;
+        for (int s = 0; s < ns; s++) total_slots += (unsigned long long)(*(volatile const uint32_t*)b.sc[s].t.count) * 8ull;
+        for (uint64_t g = tid; g < total_slots; g += nthr) {
+            // slot prefix = ray prefix / rays
+            const int s = find_scene(s_rp, ns, g * (unsigned long long)P.rays);
+            finalize_slot(b.sc[s].t, g - s_rp[s] / (unsigned long long)P.rays);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace rtsdf
+
+using namespace rtsdf;
+
+struct rtsdf_batch {
+    std::vector<rtsdf_ctx*> scenes;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // device tables
+    SceneDesc* d_desc = nullptr;
+    unsigned long long* d_vox_prefix = nullptr;
+    unsigned long long* d_tri_prefix = nullptr;
+    int2* d_big = nullptr;
+    int64_t big_cap = 0;
+    uint32_t* d_ctr = nullptr;   // big_count, bar_count, bar_gen, abort, err
+    unsigned long long* d_next_ray = nullptr;
+    BatchParams* d_params = nullptr;
+    BatchParams* h_params = nullptr;   // pinned
+    std::vector<SceneDesc> h_desc;
+    int max_passes = 0;
+    // launch configuration (autotuned)
+    int blocks_per_sm = 0;       // 0 = occupancy maximum
+    int refill_min = 4;
+    int ray_chunk = 256;
+    int use_graph = 1;
+    int barrier_spins = 0;
+    unsigned grid = 0;
+    // CUDA graph of the per-frame pipeline
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ok = false;
+    int64_t frames = 0, launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool own_stream = false;
+};
+
+namespace {
+
+rtsdf_status from_cuda_b(cudaError_t e) {
+    if (e == cudaSuccess) return RTSDF_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RTSDF_E_OOM;
+    }
+    return RTSDF_E_CUDA;
+}
+
+void drop_graph(rtsdf_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_ok = false;
+}
+
+// Rebuild the descriptor table from the scene contexts; returns true when it
+// changed (pointers move when a mesh is uploaded or a BVH rebuilt).
+cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
+    const int ns = (int)b->scenes.size();
+    std::vector<SceneDesc> desc((size_t)ns);
+    std::vector<unsigned long long> vp((size_t)ns + 1), tp((size_t)ns + 1);
+    unsigned long long av = 0, at = 0;
+    int maxp = 0;
+    memset(desc.data(), 0, sizeof(SceneDesc) * desc.size());
+    for (int s = 0; s < ns; s++) {
+        rtsdf_ctx* c = b->scenes[s];
+        SceneDesc& d = desc[s];
+        d.t.masked = c->masked;
+        d.t.count = c->d_masked_count;
+        d.t.nc = c->nc;
+        d.t.key0 = (uint32_t)c->cfg.seed;
+        d.t.key1 = (uint32_t)(c->cfg.seed >> 32);
+        d.t.bx = c->cfg.bmin[0];
+        d.t.by = c->cfg.bmin[1];
+        d.t.bz = c->cfg.bmin[2];
+        d.t.hf = c->hf;
+        d.t.wide = c->bvh.wide;
+        d.t.tri = c->bvh.tri;
+        d.t.nt = c->bvh.nt;
+        d.t.coarse = c->coarse;
+        d.t.accum = c->accum;
+        d.t.counts = c->counts;
+        d.t.fine = c->fine;
+        d.t.err = c->d_err;
+        d.t.ray_min = c->ray_min;
+        d.t.ray_cnt = c->ray_cnt;
+        d.q = c->qverts;
+        d.tris = c->tris;
+        d.n_tris = c->nt;
+        d.seeds[0] = c->seeds[0];
+        d.seeds[1] = c->seeds[1];
+        d.hc = c->hc;
+        d.beta_vox = c->cfg.beta_vox;
+        d.beta_h = c->cfg.beta_vox * c->hc;
+        d.alpha = c->cfg.alpha;
+        int L = 0;
+        while ((1 << L) < c->nc) L++;
+        d.passes = L;
+        maxp = L > maxp ? L : maxp;
+        vp[s] = av;
+        tp[s] = at;
+        av += c->nc3;
+        at += (unsigned long long)c->nt;
+    }
+    vp[ns] = av;
+    tp[ns] = at;
+    *changed = desc.size() != b->h_desc.size() ||
+               memcmp(desc.data(), b->h_desc.data(), sizeof(SceneDesc) * desc.size()) != 0 || maxp != b->max_passes;
+    if (!*changed && b->d_desc) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e) return e;
+    if (!b->d_desc) {
+        if ((e = cudaMalloc(&b->d_desc, sizeof(SceneDesc) * ns))) return e;
+        if ((e = cudaMalloc(&b->d_vox_prefix, sizeof(unsigned long long) * (ns + 1)))) return e;
+        if ((e = cudaMalloc(&b->d_tri_prefix, sizeof(unsigned long long) * (ns + 1)))) return e;
+    }
+    if ((int64_t)at > b->big_cap) {
+        if (b->d_big) cudaFree(b->d_big);
+        b->d_big = nullptr;
+        if ((e = cudaMalloc(&b->d_big, sizeof(int2) * (at > 0 ? at : 1)))) return e;
+        b->big_cap = (int64_t)at;
+    }
+    if ((e = cudaMemcpy(b->d_desc, desc.data(), sizeof(SceneDesc) * ns, cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMemcpy(b->d_vox_prefix, vp.data(), sizeof(unsigned long long) * (ns + 1), cudaMemcpyHostToDevice)))
+        return e;
+    if ((e = cudaMemcpy(b->d_tri_prefix, tp.data(), sizeof(unsigned long long) * (ns + 1), cudaMemcpyHostToDevice)))
+        return e;
+    b->h_desc = desc;
+    b->max_passes = maxp;
+    *changed = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_frame_kernel(rtsdf_batch* b) {
+    BatchArgs a;
+    a.sc = b->d_desc;
+    a.ns = (int)b->scenes.size();
+    a.params = b->d_params;
+    a.vox_prefix = b->d_vox_prefix;
+    a.tri_prefix = b->d_tri_prefix;
+    a.max_passes = b->max_passes;
+    a.big_list = b->d_big;
+    a.big_count = b->d_ctr + 0;
+    a.bar_count = b->d_ctr + 1;
+    a.bar_gen = b->d_ctr + 2;
+    a.abort = b->d_ctr + 3;
+    a.err = b->d_ctr + 4;
+    a.next_ray = b->d_next_ray;
+    a.refill_min = b->refill_min;
+    a.ray_chunk = b->ray_chunk;
+    a.spins = b->barrier_spins > 0 ? (uint32_t)b->barrier_spins : BARRIER_SPINS;
+    void* args[] = {&a};
+    b->launches++;
+    return cudaLaunchCooperativeKernel((const void*)k_batch_frame, dim3(b->grid), dim3(TRACE_THREADS), args, 0,
+                                       b->stream);
+}
+
+cudaError_t ensure_grid(rtsdf_batch* b) {
+    int sms = 0, per_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_frame, TRACE_THREADS, 0);
+    if (e) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int use = (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) ? b->blocks_per_sm : per_sm;
+    const unsigned g = (unsigned)(sms * use);
+    if (g != b->grid) {
+        b->grid = g;
+        drop_graph(b);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+rtsdf_status rtsdf_batch_create(const rtsdf_config* cfgs, int32_t n, rtsdf_batch_t* out) {
+    if (!cfgs || !out || n < 1 || n > MAX_BATCH) return RTSDF_E_ARG;
+    *out = nullptr;
+    rtsdf_batch* b = new (std::nothrow) rtsdf_batch();
+    if (!b) return RTSDF_E_OOM;
+    cudaGetDevice(&b->device);
+    // graph capture needs a stream other than the legacy default stream
+    b->stream = (cudaStream_t)cfgs[0].stream;
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return RTSDF_E_CUDA;
+        }
+        b->own_stream = true;
+    }
+    rtsdf_status st = RTSDF_OK;
+    for (int i = 0; i < n && st == RTSDF_OK; i++) {
+        rtsdf_config c = cfgs[i];
+        c.stream = b->stream;
+        rtsdf_t ctx = nullptr;
+        st = rtsdf_create(&c, &ctx);
+        if (st == RTSDF_OK) b->scenes.push_back(ctx);
+    }
+    cudaError_t e = cudaSuccess;
+    if (st == RTSDF_OK) {
+        if (!e) e = cudaMalloc(&b->d_ctr, sizeof(uint32_t) * 8);
+        if (!e) e = cudaMemset(b->d_ctr, 0, sizeof(uint32_t) * 8);
+        if (!e) e = cudaMalloc(&b->d_next_ray, sizeof(unsigned long long));
+        if (!e) e = cudaMalloc(&b->d_params, sizeof(BatchParams));
+        if (!e) e = cudaMallocHost(&b->h_params, sizeof(BatchParams));
+        if (!e) e = cudaEventCreate(&b->ev0);
+        if (!e) e = cudaEventCreate(&b->ev1);
+        if (e) st = from_cuda_b(e);
+    }
+    if (st != RTSDF_OK) {
+        rtsdf_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_batch_destroy(rtsdf_batch_t b) {
+    if (!b) return RTSDF_E_ARG;
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (rtsdf_ctx* c : b->scenes) rtsdf_destroy(c);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_vox_prefix) cudaFree(b->d_vox_prefix);
+    if (b->d_tri_prefix) cudaFree(b->d_tri_prefix);
+    if (b->d_big) cudaFree(b->d_big);
+    if (b->d_ctr) cudaFree(b->d_ctr);
+    if (b->d_next_ray) cudaFree(b->d_next_ray);
+    if (b->d_params) cudaFree(b->d_params);
+    if (b->h_params) cudaFreeHost(b->h_params);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_batch_context(rtsdf_batch_t b, int32_t i, rtsdf_t* out) {
+    if (!b || !out || i < 0 || i >= (int32_t)b->scenes.size()) return RTSDF_E_ARG;
+    *out = b->scenes[(size_t)i];
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_t b, const rtsdf_batch_tuning* t) {
+    if (!b || !t) return RTSDF_E_ARG;
+    if (t->blocks_per_sm < 0 || t->refill_min < 1 || t->refill_min > 32 || t->ray_chunk < 32 ||
+        t->ray_chunk > (1 << 20))
+        return RTSDF_E_ARG;
+    if (t->barrier_spins < 0) return RTSDF_E_ARG;
+    if (t->blocks_per_sm != b->blocks_per_sm || t->refill_min != b->refill_min || t->ray_chunk != b->ray_chunk ||
+        t->use_graph != b->use_graph || t->barrier_spins != b->barrier_spins)
+        drop_graph(b);
+    b->barrier_spins = t->barrier_spins;
+    b->blocks_per_sm = t->blocks_per_sm;
+    b->refill_min = t->refill_min;
+    b->ray_chunk = t->ray_chunk;
+    b->use_graph = t->use_graph;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_batch_get_tuning(rtsdf_batch_t b, rtsdf_batch_tuning* t) {
+    if (!b || !t) return RTSDF_E_ARG;
+    t->blocks_per_sm = b->blocks_per_sm;
+    t->refill_min = b->refill_min;
+    t->ray_chunk = b->ray_chunk;
+    t->use_graph = b->use_graph;
+    t->barrier_spins = b->barrier_spins;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_batch_frame(rtsdf_batch_t b, float d_vox, int32_t rays, int32_t frame) {
+    if (!b) return RTSDF_E_ARG;
+    if (!isfinite(d_vox) || rays < 1 || rays > 1024 || (rays & (rays - 1)) || frame < 0) return RTSDF_E_ARG;
+    for (rtsdf_ctx* c : b->scenes)
+        if (!c->have_mesh || !c->bvh.built || c->bvh_dirty || c->reset_pending) return RTSDF_E_STATE;
+    bool changed = false;
+    cudaError_t e = refresh_tables(b, &changed);
+    if (!e) e = ensure_grid(b);
+    if (e) return from_cuda_b(e);
+    if (changed) drop_graph(b);
+    // the per-frame parameters travel through a pinned host block that the
+    // graph copies to the device at its start, so one graph serves all frames
+    e = cudaStreamSynchronize(b->stream);   // the previous frame's copy has consumed h_params
+    if (e) return from_cuda_b(e);
+    int lg = 0;
+    while ((1 << lg) < rays) lg++;
+    b->h_params->frame = (uint32_t)frame;
+    b->h_params->rays = rays;
+    b->h_params->log2_rays = lg;
+    b->h_params->d_vox = d_vox;
+    if (b->use_graph && !b->graph_ok && !b->exec) {
+        // capture once: parameter copy + the persistent kernel
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (!e) {
+            // barrier words (count, generation, abort) start at zero every frame
+            cudaError_t e1 = cudaMemsetAsync(b->d_ctr + 1, 0, 3 * sizeof(uint32_t), b->stream);
+            if (!e1)
+                e1 = cudaMemcpyAsync(b->d_params, b->h_params, sizeof(BatchParams), cudaMemcpyHostToDevice, b->stream);
+            cudaError_t e2 = e1 ? e1 : launch_frame_kernel(b);
+            b->launches--;   // counted at replay
+            cudaGraph_t g = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+            if (!e2 && !e3 && g) {
+                if (cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+                    b->graph = g;
+                    b->graph_ok = true;
+                } else {
+                    cudaGraphDestroy(g);
+                }
+            } else if (g) {
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();   // a capture that the driver refused leaves no sticky error
+        if (!b->graph_ok) b->use_graph = 0;   // fall back to direct launches
+    }
+    cudaEventRecord(b->ev0, b->stream);
+    if (b->graph_ok) {
+        e = cudaGraphLaunch(b->exec, b->stream);
+        b->launches++;
+    } else {
+        e = cudaMemsetAsync(b->d_ctr + 1, 0, 3 * sizeof(uint32_t), b->stream);
+        if (!e) e = cudaMemcpyAsync(b->d_params, b->h_params, sizeof(BatchParams), cudaMemcpyHostToDevice, b->stream);
+        if (!e) e = launch_frame_kernel(b);
+    }
+    cudaEventRecord(b->ev1, b->stream);
+    if (e) return from_cuda_b(e);
+    for (rtsdf_ctx* c : b->scenes) {
+        int L = 0;
+        while ((1 << L) < c->nc) L++;
+        c->cur = L & 1;
+        c->jfa_passes = L;
+        c->voxelized = c->flooded = true;
+    }
+    b->frames++;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_batch_sync(rtsdf_batch_t b) {
+    if (!b) return RTSDF_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e) return from_cuda_b(e);
+    uint32_t ctr[5];
+    if ((e = cudaMemcpy(ctr, b->d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost))) return from_cuda_b(e);
+    if (ctr[4]) {   // the error word is read once
+        if ((e = cudaMemset(b->d_ctr + 4, 0, sizeof(uint32_t)))) return from_cuda_b(e);
+    }
+    rtsdf_status worst = RTSDF_OK;
+    if (ctr[4] & ERR_TIMEOUT) worst = RTSDF_E_TIMEOUT;
+    for (rtsdf_ctx* c : b->scenes) {
+        rtsdf_status s = rtsdf_sync(c);
+        if (s != RTSDF_OK && worst == RTSDF_OK) worst = s;
+    }
+    return worst;
+}
+
+rtsdf_status rtsdf_batch_stats(rtsdf_batch_t b, rtsdf_batch_info* out) {
+    if (!b || !out) return RTSDF_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e) return from_cuda_b(e);
+    memset(out, 0, sizeof(*out));
+    out->n_scenes = (int32_t)b->scenes.size();
+    out->grid = (int32_t)b->grid;
+    out->graph = b->graph_ok ? 1 : 0;
+    out->frames = b->frames;
+    out->launches = b->launches;
+    float ms = -1.f;
+    if (b->frames > 0 && cudaEventElapsedTime(&ms, b->ev0, b->ev1) != cudaSuccess) ms = -1.f;
+    out->last_frame_ms = ms;
+    return RTSDF_OK;
+}
+
+}  // extern "C"

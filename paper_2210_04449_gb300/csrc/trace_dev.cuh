@@ -1,0 +1,282 @@
+// Device helpers of the Sec. 2.2 tracer (ray generation, ray/triangle test,
+// 4-wide BVH traversal step), shared by the per-scene tracer (trace.cu) and
+// the batched persistent kernel.
+#pragma once
+
+#include <math_constants.h>
+
+#include "internal.cuh"
+
+namespace rtsdf {
+namespace dev {
+
+struct TraceArgs {
+    const uint32_t* masked;
+    const uint32_t* count;
+    int nc;
+    int rays, log2_rays;
+    uint32_t key0, key1, frame;
+    float bx, by, bz, hf;
+    const WNode* wide;
+    const float4* tri;
+    long long nt;
+    const float* coarse;
+    float* accum;
+    uint32_t* counts;
+    float* fine;
+    uint32_t* err;
+    TraceCounters* counters;   // work counters (counting variant only)
+    uint32_t* ray_min;         // [8 nc^3] per texel slot: min hit distance bits of this frame
+    uint32_t* ray_cnt;         // [8 nc^3] per texel slot: front | back << 16 hits of this frame
+    unsigned long long* next_ray;
+};
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ bool marsaglia(uint32_t wa, uint32_t wb, float3& d) {
+    const int A = 2 * (int)(wa >> 9) + 1 - (1 << 23);
+    const int B = 2 * (int)(wb >> 9) + 1 - (1 << 23);
+    const long long S = (long long)A * A + (long long)B * B;
+    if (S >= (1LL << 46)) return false;
+    const float s = __fmul_rn(__ll2float_rn(S), 0x1p-46f);
+    const float root = __fsqrt_rn(__fsub_rn(1.0f, s));
+    const float a = __fmul_rn(__int2float_rn(A), 0x1p-23f);
+    const float b = __fmul_rn(__int2float_rn(B), 0x1p-23f);
+    d.x = __fmul_rn(__fmul_rn(2.0f, a), root);
+    d.y = __fmul_rn(__fmul_rn(2.0f, b), root);
+    d.z = __fsub_rn(1.0f, __fmul_rn(2.0f, s));
+    return true;
+}
+
+__device__ __forceinline__ float3 sphere_dir(uint32_t k0, uint32_t k1, uint32_t texel, uint32_t frame,
+                                             uint32_t ray) {
+    float3 d;
+    for (uint32_t draw = 0; draw < 8; draw++) {
+        uint32_t c[4] = {draw, ray, frame, texel};
+        philox4x32_10(c, k0, k1);
+        if (marsaglia(c[0], c[1], d)) return d;
+        if (marsaglia(c[2], c[3], d)) return d;
+    }
+    return make_float3(0.f, 0.f, 1.f);
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+    return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                       __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+
+// Moller-Trumbore, closed triangle, t >= 0.  Returns hit; t and front out.
+__device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 v0, float3 e1, float3 e2, float& t,
+                                       bool& front) {
+    const float3 p = cross3(d, e2);
+    const float det = dot3(e1, p);
+    if (det == 0.0f) return false;
+    const float inv = __fdiv_rn(1.0f, det);
+    const float3 tv = make_float3(__fsub_rn(o.x, v0.x), __fsub_rn(o.y, v0.y), __fsub_rn(o.z, v0.z));
+    const float u = __fmul_rn(dot3(tv, p), inv);
+    if (!(u >= 0.0f && u <= 1.0f)) return false;
+    const float3 q = cross3(tv, e1);
+    const float v = __fmul_rn(dot3(d, q), inv);
+    if (!(v >= 0.0f && __fadd_rn(u, v) <= 1.0f)) return false;
+    const float tt = __fmul_rn(dot3(e2, q), inv);
+    if (!(tt >= 0.0f)) return false;
+    t = tt;
+    front = det > 0.0f;
+    return true;
+}
+
+__device__ __forceinline__ float safe_inv(float d) {
+    return __fdiv_rn(1.0f, fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
+}
+
+// Per-lane ray state of the persistent tracer.
+struct Ray {
+    float3 o, d, id, oid;
+    float bt;          // closest hit distance so far
+    int bidx;          // its original triangle index (0x7FFFFFFF: none)
+    bool bfront;
+    int node;          // next node to enter (>= 0 internal, < 0 ~leaf)
+    int sp;
+    uint32_t slot;     // texel slot = 8 * (masked-list position) + child
+    uint32_t steps;    // nodes entered; a tree of 2 nt - 1 nodes bounds it
+};
+
+__device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r) {
+    const uint32_t slot = (uint32_t)(g >> a.log2_rays);
+    const uint32_t ray = (uint32_t)(g & (uint64_t)(a.rays - 1));
+    const uint32_t parent = a.masked[slot >> 3];
+    const uint32_t ch = slot & 7u;
+    const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
+    const uint32_t px = parent % nc, py = (parent / nc) % nc, pz = parent / (nc * nc);
+    const uint32_t jx = 2 * px + (ch & 1), jy = 2 * py + ((ch >> 1) & 1), jz = 2 * pz + (ch >> 2);
+    const uint32_t texel = jx + nf * (jy + nf * jz);
+    r.o = make_float3(__fadd_rn(a.bx, __fmul_rn(__fadd_rn((float)jx, 0.5f), a.hf)),
+                      __fadd_rn(a.by, __fmul_rn(__fadd_rn((float)jy, 0.5f), a.hf)),
+                      __fadd_rn(a.bz, __fmul_rn(__fadd_rn((float)jz, 0.5f), a.hf)));
+    r.d = sphere_dir(a.key0, a.key1, texel, a.frame, ray);
+    r.id = make_float3(safe_inv(r.d.x), safe_inv(r.d.y), safe_inv(r.d.z));
+    r.oid = make_float3(r.o.x * r.id.x, r.o.y * r.id.y, r.o.z * r.id.z);
+    r.bt = CUDART_INF_F;
+    r.bidx = 0x7FFFFFFF;
+    r.bfront = false;
+    r.node = a.nt > 1 ? 0 : ~0;
+    r.sp = 0;
+    r.slot = slot;
+    r.steps = 0;
+}
+
+// One traversal step (enter one node or test one leaf).  Returns true when
+// the ray's traversal is complete.
+constexpr int TRACE_THREADS = 128;
+constexpr int SMEM_STACK = 24;
+
+struct Stack {
+    int* id;      // &s_id[0][thread], stride TRACE_THREADS
+    float* t;     // &s_t[0][thread]
+    int2* deep;   // local overflow
+    __device__ __forceinline__ void push(int sp, int node, float t0) {
+        if (sp < SMEM_STACK) {
+            id[sp * TRACE_THREADS] = node;
+            t[sp * TRACE_THREADS] = t0;
+        } else {
+            deep[sp - SMEM_STACK] = make_int2(node, __float_as_int(t0));
+        }
+    }
+    __device__ __forceinline__ void pop(int sp, int& node, float& t0) const {
+        if (sp < SMEM_STACK) {
+            node = id[sp * TRACE_THREADS];
+            t0 = t[sp * TRACE_THREADS];
+        } else {
+            const int2 e = deep[sp - SMEM_STACK];
+            node = e.x;
+            t0 = __int_as_float(e.y);
+        }
+    }
+};
+
+// A: any argument block with the BVH fields wide, tri, nt and err.
+template <bool COUNT, class A>
+__device__ __forceinline__ bool step_ray(const A& a, Ray& r, Stack& stack, uint32_t& visits, uint32_t& tests) {
+    if (COUNT) visits++;
+    if (++r.steps > 2u * (uint32_t)a.nt + 2u) {   // only a damaged tree gets here
+        atomicOr(a.err, ERR_STACK);
+        return true;
+    }
+    const int node = r.node;
+    if (node >= 0) {
+        // 4-wide node: test the four child boxes, visit the nearest hit child
+        // next and push the others farthest-first with their entry distance
+        const WNode* w = a.wide + node;
+        const float4 lx = __ldg(&w->lox), hx = __ldg(&w->hix);
+        const float4 ly = __ldg(&w->loy), hy = __ldg(&w->hiy);
+        const float4 lz = __ldg(&w->loz), hz = __ldg(&w->hiz);
+        const int4 ch = __ldg(&w->child);
+        float key[4];
+        int val[4] = {ch.x, ch.y, ch.z, ch.w};
+        const float blx[4] = {lx.x, lx.y, lx.z, lx.w}, bhx[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float bly[4] = {ly.x, ly.y, ly.z, ly.w}, bhy[4] = {hy.x, hy.y, hy.z, hy.w};
+        const float blz[4] = {lz.x, lz.y, lz.z, lz.w}, bhz[4] = {hz.x, hz.y, hz.z, hz.w};
+        int nh = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float x0 = fmaf(blx[k], r.id.x, -r.oid.x), x1 = fmaf(bhx[k], r.id.x, -r.oid.x);
+            const float y0 = fmaf(bly[k], r.id.y, -r.oid.y), y1 = fmaf(bhy[k], r.id.y, -r.oid.y);
+            const float z0 = fmaf(blz[k], r.id.z, -r.oid.z), z1 = fmaf(bhz[k], r.id.z, -r.oid.z);
+            const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.f));
+            const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), r.bt));
+            const bool hit = t0 <= t1 && val[k] != WIDE_EMPTY;
+            key[k] = hit ? t0 : CUDART_INF_F;
+            nh += hit;
+        }
+        if (nh > 0) {
+            // ascending sort of (key, val): a 5-exchange network
+#define RTSDF_CAS(i, j)                                                     \
+    if (key[j] < key[i]) {                                                  \
+        const float tk = key[i]; key[i] = key[j]; key[j] = tk;              \
+        const int tv = val[i]; val[i] = val[j]; val[j] = tv;                \
+    }
+            RTSDF_CAS(0, 1) RTSDF_CAS(2, 3) RTSDF_CAS(0, 2) RTSDF_CAS(1, 3) RTSDF_CAS(1, 2)
+#undef RTSDF_CAS
+#pragma unroll
+            for (int k = 3; k >= 1; k--) {
+                if (k < nh) {
+                    if (r.sp < TRACE_STACK) stack.push(r.sp++, val[k], key[k]);
+                    else atomicOr(a.err, ERR_STACK);
+                }
+            }
+            r.node = val[0];
+            return false;
+        }
+    } else {
+        if (COUNT) tests++;
+        const int leaf = ~node;
+        const float4 p0 = __ldg(&a.tri[3 * leaf]);
+        const float4 p1 = __ldg(&a.tri[3 * leaf + 1]);
+        const float4 p2 = __ldg(&a.tri[3 * leaf + 2]);
+        float t;
+        bool fr;
+        if (ray_tri(r.o, r.d, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                    make_float3(p2.x, p2.y, p2.z), t, fr)) {
+            const int idx = __float_as_int(p0.w);
+            if (t < r.bt || (t == r.bt && idx < r.bidx)) {
+                r.bt = t;
+                r.bidx = idx;
+                r.bfront = fr;
+            }
+        }
+    }
+    // pop the next entry that can still hold a hit at distance <= bt
+    while (r.sp > 0) {
+        int nx;
+        float te;
+        stack.pop(--r.sp, nx, te);
+        if (te <= r.bt) {
+            r.node = nx;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Eq. 1 for one texel slot after its rays committed: u_t = min(u, r_t) (the
+// alpha decay was applied by the mask stage), counts += this frame's hits
+// (saturating at 16 bits), f_t = +-u_t or c_t while no ray has hit; the
+// slot's scratch is cleared for the next frame.
+__device__ __forceinline__ void finalize_slot(const TraceArgs& a, uint64_t s) {
+    const uint32_t parent = a.masked[s >> 3];
+    const uint32_t ch = (uint32_t)(s & 7);
+    const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
+    const uint32_t px = parent % nc, py = (parent / nc) % nc, pz = parent / (nc * nc);
+    const uint32_t texel = (2 * px + (ch & 1)) + nf * ((2 * py + ((ch >> 1) & 1)) + nf * (2 * pz + (ch >> 2)));
+    const float rmin = __uint_as_float(a.ray_min[s]);
+    const uint32_t cv = a.ray_cnt[s];
+    a.ray_min[s] = 0x7F800000u;
+    a.ray_cnt[s] = 0u;
+    const float u = fminf(a.accum[texel], rmin);
+    const uint32_t cw = a.counts[texel];
+    const uint32_t f = min((cw & 0xFFFFu) + (cv & 0xFFFFu), 0xFFFFu);
+    const uint32_t b = min((cw >> 16) + (cv >> 16), 0xFFFFu);
+    a.accum[texel] = u;
+    a.counts[texel] = f | (b << 16);
+    const float mag = u == CUDART_INF_F ? a.coarse[parent] : u;
+    a.fine[texel] = b > f ? -mag : mag;
+}
+
+}  // namespace dev
+}  // namespace rtsdf
