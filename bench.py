@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rtsdf", choices=["rtsdf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--objects", type=int, default=N_OBJ, help="sphere count (500 = the 1M-triangle workload)")
     ap.add_argument("--coarse-n", type=int, default=NC, help="coarse grid size (256 = the benchmark workload; "
                                                               "smaller only for profiling captures)")
@@ -153,6 +154,9 @@ def run_gpu(args, rank, world):
         rt.trace(D_VOX, RAYS, t)
 
     frame(0, None)
+    # launch parameters from the autotuner (untimed; the accumulated SDF is
+    # saved and restored by it)
+    tuning = rt.autotune(D_VOX, RAYS, 1, use_cache=True)
     for t in range(1, args.warmup + 1):
         frame(t, trans_dev[t])
     rt.sync()
@@ -209,6 +213,10 @@ def run_gpu(args, rank, world):
         rt.masked_count()
         rt.sync()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+
+    # Sec. 2.3 on the frame's fine SDF: 1920x1080 floor points, one light,
+    # k = 8, 64 steps (forward) and the adjoint at 1024x1024
+    shadow = time_shadow(rt, dev)
 
     rays_frame = n_masked_tex * RAYS
     trace_ms = stage["trace"]
@@ -274,9 +282,110 @@ def run_gpu(args, rank, world):
         "clocks": clk,
         "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": N_OBJ * 3 * 4,
                 "d2h_bytes_per_step": 8 + 4},
+        "shadow": shadow,
+        "tuning": tuning,
     }
     rt.close()
     return line, n_masked_tex
+
+
+def time_shadow(rt, dev, reps=5):
+    """Shadow forward (1920x1080) and adjoint (1024x1024) on the context's
+    fine SDF, CUDA events over `reps` launches each."""
+    import torch
+
+    from synth import scenes as S
+    out = {}
+    L = (0.4, 1.0, 0.3)
+    for name, (w, h) in (("forward", (1920, 1080)), ("backward", (1024, 1024))):
+        pos, nrm = S.floor_gbuffer(w, h, y=0.02)
+        pos_t, nrm_t = torch.tensor(pos, device=dev), torch.tensor(nrm, device=dev)
+        vis = torch.empty((h, w), device=dev)
+        if name == "backward":
+            dvis = torch.full((h, w), 1.0 / (w * h), device=dev)
+            dsdf = torch.zeros(rt.fine_n ** 3, device=dev)
+            dl = torch.zeros(3, device=dev)
+
+        def once():
+            if name == "forward":
+                rt.shadow(pos_t, nrm_t, L, k=8.0, steps=64, out=vis)
+            else:
+                rt.shadow_backward(pos_t, nrm_t, L, dvis, dsdf, dl, k=8.0, steps=64)
+        once()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            once()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": round(ms, 4), "points": w * h, "points_per_s": round(w * h / (ms * 1e-3))}
+    rt.sync()
+    return out
+
+
+def run_batched(dev, frames=3, rays=32, d_vox=2.0):
+    """The batched form against plain per-scene frames on 64 uneven scenes
+    (coarse 32..128, 1k-200k triangles): ms/frame for all scenes, and whether
+    the two give identical fine grids."""
+    import numpy as np
+    import torch
+
+    from paper_2210_04449_gb300 import RTSDF, RTSDFBatch
+    from synth import scenes as S
+    meshes = S.batch_scenes(3, 64)
+    cfgs = [dict(coarse_n=m.meta["coarse_n"], beta_vox=BETA, seed=100 + i) for i, m in enumerate(meshes)]
+    # plain: one context per scene, frames run scene after scene
+    ctxs = []
+    for c, m in zip(cfgs, meshes):
+        rt = RTSDF(**c)
+        rt.upload_mesh(m.verts, m.tris)
+        rt.build_bvh()
+        ctxs.append(rt)
+    stream = torch.cuda.current_stream(dev)
+
+    def plain_frame(f):
+        for rt in ctxs:
+            rt.update(d_vox, rays, f)
+    plain_frame(0)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for f in range(1, frames + 1):
+        plain_frame(f)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1) / frames
+    ref = [float(rt.grids()["fine"].double().sum().item()) for rt in ctxs]
+    for rt in ctxs:
+        rt.close()
+    del ctxs
+    torch.cuda.empty_cache()
+    # batched
+    b = RTSDFBatch(cfgs)
+    for sc, m in zip(b.scenes, meshes):
+        sc.upload_mesh(m.verts, m.tris)
+        sc.build_bvh()
+    b.frame(d_vox, rays, 0)
+    b.sync()
+    tuned = b.autotune(d_vox, rays, 1, use_cache=True)
+    t0 = time.perf_counter()
+    ms = []
+    for f in range(1, frames + 1):
+        b.frame(d_vox, rays, f)
+        b.sync()
+        ms.append(b.stats()["last_frame_ms"])
+    wall = (time.perf_counter() - t0) * 1e3 / frames
+    got = [float(sc.grids()["fine"].double().sum().item()) for sc in b.scenes]
+    info = b.stats()
+    b.close()
+    tris = sum(m.nt for m in meshes)
+    return {"workload": f"64 scenes, coarse 32..128, {tris:,} tris total, {rays} rays/texel",
+            "plain_ms_per_frame": round(plain_ms, 3), "batched_ms_per_frame": round(float(np.mean(ms)), 3),
+            "batched_wall_ms_per_frame": round(wall, 3), "speedup": round(plain_ms / float(np.mean(ms)), 3),
+            "identical": bool(np.array_equal(np.array(ref), np.array(got))), "graph": bool(info["graph"]),
+            "grid": info["grid"], "tuning": tuned, "launches_per_frame": 1}
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -356,6 +465,9 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     line, m_tex = run_gpu(args, rank, world)
+    if not args.no_batch:
+        import torch
+        line["batched"] = run_batched(torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             ms, info = oracle_frame_sample(16, masked_texels=m_tex)

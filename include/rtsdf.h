@@ -250,6 +250,36 @@ rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_t batch, const rtsdf_batch_tunin
 rtsdf_status rtsdf_batch_get_tuning(rtsdf_batch_t batch, rtsdf_batch_tuning* t);
 rtsdf_status rtsdf_batch_stats(rtsdf_batch_t batch, rtsdf_batch_info* out);
 
+/* Launch parameters of the per-scene path (picked by rtsdf_autotune). */
+typedef struct {
+    int32_t jfa_tile;            /* jump-flood block tile: 0 = 32x8, 1 = 64x4, 2 = 128x2, 3 = 32x4 voxels */
+    int32_t trace_blocks_per_sm; /* persistent tracer blocks per SM (0 = occupancy maximum) */
+    int32_t refill_min;          /* tracer: refill a warp once this many lanes are idle (1..32) */
+    int32_t ray_chunk;           /* tracer: rays a warp takes from the global counter at a time */
+} rtsdf_tuning;
+
+rtsdf_status rtsdf_set_tuning(rtsdf_t ctx, const rtsdf_tuning* t);
+rtsdf_status rtsdf_get_tuning(rtsdf_t ctx, rtsdf_tuning* t);
+
+/* Autotuner of the per-scene path: times candidate tunings (CUDA events) on
+ * the context's current scene -- jump-flood tiles on rtsdf_jfa, then the
+ * tracer's blocks per SM, refill threshold and ray chunk on rtsdf_trace(
+ * d_vox, rays, frame) -- keeps the fastest and returns it in best.  The
+ * temporal state is saved before and restored after, so the accumulated
+ * fine SDF is unchanged.  Results are cached per (device, coarse_n,
+ * log2 triangles); use_cache != 0 returns a cached entry without timing.
+ * Requires a mesh and a current BVH; synchronises; allocates a temporary
+ * copy of the fine grids. */
+rtsdf_status rtsdf_autotune(rtsdf_t ctx, float d_vox, int32_t rays_per_texel, int32_t frame, int32_t use_cache,
+                            rtsdf_tuning* best);
+
+/* Autotuner of the batched form: blocks per SM, refill threshold and ray
+ * chunk of the persistent launch, timed on rtsdf_batch_frame with every
+ * scene's temporal state saved and restored.  Cached per (device, scenes,
+ * log2 voxels, log2 triangles). */
+rtsdf_status rtsdf_batch_autotune(rtsdf_batch_t batch, float d_vox, int32_t rays_per_texel, int32_t frame,
+                                  int32_t use_cache, rtsdf_batch_tuning* best);
+
 /* Borrowed device views of the grids (no synchronisation). */
 rtsdf_status rtsdf_get_grids(rtsdf_t ctx, rtsdf_grids* out);
 

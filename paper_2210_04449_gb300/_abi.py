@@ -43,6 +43,10 @@ class BatchTuning(ctypes.Structure):
                 ("barrier_spins", c_i32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("jfa_tile", c_i32), ("trace_blocks_per_sm", c_i32), ("refill_min", c_i32), ("ray_chunk", c_i32)]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_scenes", c_i32), ("grid", c_i32), ("graph", c_i32), ("frames", c_i64), ("launches", c_i64),
                 ("last_frame_ms", c_f)]
@@ -75,6 +79,10 @@ SIGNATURES = {
     "rtsdf_batch_set_tuning": (status_t, [c_vp, ctypes.POINTER(BatchTuning)]),
     "rtsdf_batch_get_tuning": (status_t, [c_vp, ctypes.POINTER(BatchTuning)]),
     "rtsdf_batch_stats": (status_t, [c_vp, ctypes.POINTER(BatchInfo)]),
+    "rtsdf_set_tuning": (status_t, [ctx_t, ctypes.POINTER(Tuning)]),
+    "rtsdf_get_tuning": (status_t, [ctx_t, ctypes.POINTER(Tuning)]),
+    "rtsdf_autotune": (status_t, [ctx_t, c_f, c_i32, c_i32, c_i32, ctypes.POINTER(Tuning)]),
+    "rtsdf_batch_autotune": (status_t, [c_vp, c_f, c_i32, c_i32, c_i32, ctypes.POINTER(BatchTuning)]),
     "rtsdf_get_grids": (status_t, [ctx_t, ctypes.POINTER(Grids)]),
     "rtsdf_get_masked_count": (status_t, [ctx_t, ctypes.POINTER(c_i64)]),
     "rtsdf_get_stats": (status_t, [ctx_t, ctypes.POINTER(Stats)]),

@@ -205,6 +205,25 @@ class RTSDF:
     def set_profiling(self, on: bool) -> None:
         call("rtsdf_set_profiling", self._h, int(bool(on)))
 
+    def get_tuning(self) -> dict:
+        t = _abi.Tuning()
+        call("rtsdf_get_tuning", self._h, ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in _abi.Tuning._fields_}
+
+    def set_tuning(self, **kw) -> None:
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = _abi.Tuning(**cur)
+        call("rtsdf_set_tuning", self._h, ctypes.byref(t))
+
+    def autotune(self, d_vox: float, rays_per_texel: int, frame: int, use_cache: bool = True) -> dict:
+        """Time candidate launch parameters on this scene and keep the fastest
+        (the accumulated SDF is saved and restored)."""
+        t = _abi.Tuning()
+        call("rtsdf_autotune", self._h, float(d_vox), int(rays_per_texel), int(frame), int(bool(use_cache)),
+             ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in _abi.Tuning._fields_}
+
     def set_counting(self, on: bool) -> None:
         call("rtsdf_set_counting", self._h, int(bool(on)))
 
@@ -275,6 +294,12 @@ class RTSDFBatch:
         cur.update(kw)
         t = _abi.BatchTuning(**cur)
         call("rtsdf_batch_set_tuning", self._h, ctypes.byref(t))
+
+    def autotune(self, d_vox: float, rays_per_texel: int, frame: int, use_cache: bool = True) -> dict:
+        t = _abi.BatchTuning()
+        call("rtsdf_batch_autotune", self._h, float(d_vox), int(rays_per_texel), int(frame), int(bool(use_cache)),
+             ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in _abi.BatchTuning._fields_}
 
     def stats(self) -> dict:
         s = _abi.BatchInfo()

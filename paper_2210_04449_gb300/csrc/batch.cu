@@ -18,9 +18,13 @@
 // blocks are resident, so the bound only guards against a broken launch.
 #include <math.h>
 #include <math_constants.h>
+#include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -44,6 +48,7 @@ struct SceneDesc {
     uint32_t* seeds[2];
     float hc, beta_h, beta_vox, alpha;
     int passes;
+    int wide_off, tri_off;    // this scene's nodes / leaves in the concatenated BVH
 };
 
 struct BatchParams {
@@ -76,6 +81,7 @@ struct BatchArgs {
     int refill_min;
     int ray_chunk;
     uint32_t spins;
+    BvhRef bvh;               // every scene's BVH in one array (child ids rebased)
 };
 
 __device__ __forceinline__ int find_scene(const unsigned long long* prefix, int ns, unsigned long long g) {
@@ -117,7 +123,7 @@ __device__ bool grid_barrier(const BatchArgs& b) {
     return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(TRACE_THREADS, 6) k_batch_frame(BatchArgs b) {
+__global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint64_t nthr = gridDim.x * (uint64_t)blockDim.x;
     const BatchParams P = *b.params;
@@ -285,7 +291,6 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_batch_frame(BatchArgs b) {
         int2 deep[TRACE_STACK - SMEM_STACK];
         Stack stk{&s_id[0][threadIdx.x], &s_t[0][threadIdx.x], deep};
         Ray r;
-        BvhRef bv{nullptr, nullptr, 0, b.err};
         int scene = 0;
         bool active = false;
         unsigned long long chunk_next = 0, chunk_end = 0;
@@ -318,9 +323,9 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_batch_frame(BatchArgs b) {
                         ta.log2_rays = P.log2_rays;
                         ta.frame = P.frame;
                         setup_ray(ta, g - s_rp[scene], r);
-                        bv.wide = ta.wide;
-                        bv.tri = ta.tri;
-                        bv.nt = ta.nt;
+                        // enter the scene's root in the concatenated tree
+                        const SceneDesc& sd = b.sc[scene];
+                        r.node = ta.nt > 1 ? sd.wide_off : (ta.nt == 1 ? ~sd.tri_off : WIDE_EMPTY);
                         active = true;
                     }
                 }
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_batch_frame(BatchArgs b) {
             if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
             for (;;) {
                 bool done = false;
-                if (active) done = step_ray<false>(bv, r, stk, dummy_v, dummy_t);
+                if (active) done = step_ray<false>(b.bvh, r, stk, dummy_v, dummy_t);
                 const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
                 if (fin && done) {
                     const unsigned long long key = ((unsigned long long)scene << 32) | r.slot;
@@ -366,6 +371,21 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_batch_frame(BatchArgs b) {
     }
 }
 
+// Copy one scene's 4-wide nodes into the concatenated array, rebasing child
+// ids (internal by the scene's node offset, leaves by its leaf offset).
+__global__ void k_rebase_nodes(const WNode* __restrict__ src, WNode* __restrict__ dst, int64_t n, int wide_off,
+                               int tri_off) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    WNode w = src[i];
+    int* ch = &w.child.x;
+    for (int k = 0; k < 4; k++) {
+        if (ch[k] == WIDE_EMPTY) continue;
+        ch[k] = ch[k] >= 0 ? ch[k] + wide_off : ~((~ch[k]) + tri_off);
+    }
+    dst[wide_off + i] = w;
+}
+
 }  // namespace
 }  // namespace rtsdf
 
@@ -381,6 +401,9 @@ struct rtsdf_batch {
     unsigned long long* d_tri_prefix = nullptr;
     int2* d_big = nullptr;
     int64_t big_cap = 0;
+    WNode* d_wide_all = nullptr;     // all scenes' nodes
+    float4* d_tri_all = nullptr;     // all scenes' leaf triangles
+    int64_t wide_cap = 0, tri_cap = 0, total_nt = 0;
     uint32_t* d_ctr = nullptr;   // big_count, bar_count, bar_gen, abort, err
     unsigned long long* d_next_ray = nullptr;
     BatchParams* d_params = nullptr;
@@ -473,6 +496,13 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
     }
     vp[ns] = av;
     tp[ns] = at;
+    int64_t wo = 0, to = 0;
+    for (int s = 0; s < ns; s++) {
+        desc[s].wide_off = (int)wo;
+        desc[s].tri_off = (int)to;
+        wo += b->scenes[s]->bvh.n_wide;
+        to += b->scenes[s]->bvh.nt;
+    }
     *changed = desc.size() != b->h_desc.size() ||
                memcmp(desc.data(), b->h_desc.data(), sizeof(SceneDesc) * desc.size()) != 0 || maxp != b->max_passes;
     if (!*changed && b->d_desc) return cudaSuccess;
@@ -489,6 +519,35 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
         if ((e = cudaMalloc(&b->d_big, sizeof(int2) * (at > 0 ? at : 1)))) return e;
         b->big_cap = (int64_t)at;
     }
+    // concatenated BVH of all scenes
+    if (wo > b->wide_cap) {
+        if (b->d_wide_all) cudaFree(b->d_wide_all);
+        b->d_wide_all = nullptr;
+        if ((e = cudaMalloc(&b->d_wide_all, sizeof(WNode) * (wo > 0 ? wo : 1)))) return e;
+        b->wide_cap = wo;
+    }
+    if (to > b->tri_cap) {
+        if (b->d_tri_all) cudaFree(b->d_tri_all);
+        b->d_tri_all = nullptr;
+        if ((e = cudaMalloc(&b->d_tri_all, sizeof(float4) * 3 * (to > 0 ? to : 1)))) return e;
+        b->tri_cap = to;
+    }
+    b->total_nt = to;
+    for (int s = 0; s < ns; s++) {
+        const Bvh& bv = b->scenes[s]->bvh;
+        if (bv.n_wide > 0) {
+            k_rebase_nodes<<<(unsigned)((bv.n_wide + 255) / 256), 256, 0, b->stream>>>(bv.wide, b->d_wide_all,
+                                                                                     bv.n_wide, desc[s].wide_off,
+                                                                                     desc[s].tri_off);
+            b->launches++;
+        }
+        if (bv.nt > 0 &&
+            (e = cudaMemcpyAsync(b->d_tri_all + 3 * (int64_t)desc[s].tri_off, bv.tri, sizeof(float4) * 3 * bv.nt,
+                                 cudaMemcpyDeviceToDevice, b->stream)))
+            return e;
+    }
+    if ((e = cudaGetLastError())) return e;
+    if ((e = cudaStreamSynchronize(b->stream))) return e;
     if ((e = cudaMemcpy(b->d_desc, desc.data(), sizeof(SceneDesc) * ns, cudaMemcpyHostToDevice))) return e;
     if ((e = cudaMemcpy(b->d_vox_prefix, vp.data(), sizeof(unsigned long long) * (ns + 1), cudaMemcpyHostToDevice)))
         return e;
@@ -518,6 +577,10 @@ cudaError_t launch_frame_kernel(rtsdf_batch* b) {
     a.refill_min = b->refill_min;
     a.ray_chunk = b->ray_chunk;
     a.spins = b->barrier_spins > 0 ? (uint32_t)b->barrier_spins : BARRIER_SPINS;
+    a.bvh.wide = b->d_wide_all;
+    a.bvh.tri = b->d_tri_all;
+    a.bvh.nt = b->total_nt;
+    a.bvh.err = b->d_ctr + 4;
     void* args[] = {&a};
     b->launches++;
     return cudaLaunchCooperativeKernel((const void*)k_batch_frame, dim3(b->grid), dim3(TRACE_THREADS), args, 0,
@@ -594,6 +657,8 @@ rtsdf_status rtsdf_batch_destroy(rtsdf_batch_t b) {
     if (b->d_vox_prefix) cudaFree(b->d_vox_prefix);
     if (b->d_tri_prefix) cudaFree(b->d_tri_prefix);
     if (b->d_big) cudaFree(b->d_big);
+    if (b->d_wide_all) cudaFree(b->d_wide_all);
+    if (b->d_tri_all) cudaFree(b->d_tri_all);
     if (b->d_ctr) cudaFree(b->d_ctr);
     if (b->d_next_ray) cudaFree(b->d_next_ray);
     if (b->d_params) cudaFree(b->d_params);
@@ -741,3 +806,147 @@ rtsdf_status rtsdf_batch_stats(rtsdf_batch_t b, rtsdf_batch_info* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched form (see rtsdf_batch_autotune in rtsdf.h).
+namespace {
+
+std::mutex g_bt_mutex;
+std::map<std::string, rtsdf_batch_tuning> g_bt_cache;
+
+struct BatchSnapshot {
+    std::vector<void*> bufs;
+    cudaError_t take(rtsdf_batch* b) {
+        for (rtsdf_ctx* c : b->scenes) {
+            const size_t bytes = c->nf3 * 4;
+            for (int k = 0; k < 3; k++) {
+                void* p = nullptr;
+                cudaError_t e = cudaMalloc(&p, bytes);
+                if (e) return e;
+                bufs.push_back(p);
+                const void* src = k == 0 ? (const void*)c->accum : k == 1 ? (const void*)c->counts : (const void*)c->fine;
+                if ((e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyDeviceToDevice, b->stream))) return e;
+            }
+        }
+        return cudaSuccess;
+    }
+    cudaError_t restore(rtsdf_batch* b) const {
+        size_t i = 0;
+        for (rtsdf_ctx* c : b->scenes) {
+            const size_t bytes = c->nf3 * 4;
+            void* dst[3] = {c->accum, c->counts, c->fine};
+            for (int k = 0; k < 3; k++) {
+                cudaError_t e = cudaMemcpyAsync(dst[k], bufs[i++], bytes, cudaMemcpyDeviceToDevice, b->stream);
+                if (e) return e;
+            }
+        }
+        return cudaSuccess;
+    }
+    ~BatchSnapshot() {
+        for (void* p : bufs) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+extern "C" rtsdf_status rtsdf_batch_autotune(rtsdf_batch_t b, float d_vox, int32_t rays, int32_t frame,
+                                             int32_t use_cache, rtsdf_batch_tuning* best) {
+    if (!b) return RTSDF_E_ARG;
+    unsigned long long vox = 0, tris = 0;
+    for (rtsdf_ctx* c : b->scenes) {
+        vox += c->nc3;
+        tris += (unsigned long long)c->nt;
+    }
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, b->device);
+    int lv = 0, lt = 0;
+    while ((1ull << lv) < vox) lv++;
+    while ((1ull << lt) < tris) lt++;
+    char kbuf[320];
+    snprintf(kbuf, sizeof(kbuf), "%s|%zu|%d|%d", prop.name, b->scenes.size(), lv, lt);
+    const std::string key = kbuf;
+    rtsdf_batch_tuning cur;
+    rtsdf_batch_get_tuning(b, &cur);
+    if (use_cache) {
+        std::lock_guard<std::mutex> lock(g_bt_mutex);
+        auto it = g_bt_cache.find(key);
+        if (it != g_bt_cache.end()) {
+            rtsdf_status s = rtsdf_batch_set_tuning(b, &it->second);
+            if (s == RTSDF_OK && best) *best = it->second;
+            return s;
+        }
+    }
+    BatchSnapshot snap;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (!e) e = snap.take(b);
+    if (e) return from_cuda_b(e);
+    // one warm frame (graph capture) and one timed frame per candidate, both
+    // from the saved state
+    auto trial = [&](const rtsdf_batch_tuning& t, float* ms) -> rtsdf_status {
+        rtsdf_status s = rtsdf_batch_set_tuning(b, &t);
+        for (int rep = 0; rep < 2 && s == RTSDF_OK; rep++) {
+            cudaError_t r = snap.restore(b);
+            if (r) return from_cuda_b(r);
+            s = rtsdf_batch_frame(b, d_vox, rays, frame);
+            if (s == RTSDF_OK) s = rtsdf_batch_sync(b);
+        }
+        if (s != RTSDF_OK) return s;
+        float v = 0.f;
+        if (cudaEventElapsedTime(&v, b->ev0, b->ev1) != cudaSuccess) return RTSDF_E_CUDA;
+        *ms = v;
+        return RTSDF_OK;
+    };
+    float base = 0.f;
+    rtsdf_status st = trial(cur, &base);
+    const int refills[] = {2, 4, 8, 16};
+    for (int r : refills) {
+        if (st != RTSDF_OK || r == cur.refill_min) continue;
+        rtsdf_batch_tuning t = cur;
+        t.refill_min = r;
+        float ms = 0.f;
+        st = trial(t, &ms);
+        if (st == RTSDF_OK && ms < base) {
+            base = ms;
+            cur = t;
+        }
+    }
+    const int chunks[] = {64, 256, 1024};
+    for (int ch : chunks) {
+        if (st != RTSDF_OK || ch == cur.ray_chunk) continue;
+        rtsdf_batch_tuning t = cur;
+        t.ray_chunk = ch;
+        float ms = 0.f;
+        st = trial(t, &ms);
+        if (st == RTSDF_OK && ms < base) {
+            base = ms;
+            cur = t;
+        }
+    }
+    int per_sm = 0;
+    if (st == RTSDF_OK &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_frame, TRACE_THREADS, 0) != cudaSuccess)
+        st = RTSDF_E_CUDA;
+    for (int blocks = per_sm - 1; blocks >= per_sm - 2 && blocks >= 1 && st == RTSDF_OK; blocks--) {
+        rtsdf_batch_tuning t = cur;
+        t.blocks_per_sm = blocks;
+        float ms = 0.f;
+        st = trial(t, &ms);
+        if (st == RTSDF_OK && ms < base) {
+            base = ms;
+            cur = t;
+        }
+    }
+    rtsdf_status s2 = rtsdf_batch_set_tuning(b, &cur);
+    cudaError_t r = snap.restore(b);
+    if (!r) r = cudaStreamSynchronize(b->stream);
+    if (st != RTSDF_OK) return st;
+    if (s2 != RTSDF_OK) return s2;
+    if (r) return from_cuda_b(r);
+    {
+        std::lock_guard<std::mutex> lock(g_bt_mutex);
+        g_bt_cache[key] = cur;
+    }
+    if (best) *best = cur;
+    return RTSDF_OK;
+}

@@ -140,6 +140,9 @@ struct rtsdf_ctx {
     unsigned long long* d_next_ray = nullptr;
     unsigned trace_grid = 0;
 
+    // launch parameters (rtsdf_set_tuning / rtsdf_autotune)
+    rtsdf_tuning tune = {0, 0, 4, 256};
+
     rtsdf::Bvh bvh;
     bool bvh_dirty = true;
 
@@ -178,6 +181,9 @@ cudaError_t launch_shadow_bwd(rtsdf_ctx* c, const float* sdf, const float* pos, 
                               int64_t npix, const float L[3], float inv_norm, float k, int steps,
                               float smax, float eps, const float* dvis, float* dsdf,
                               float* dlight);
+
+// Resident blocks per SM of the per-scene tracer kernel.
+cudaError_t trace_occupancy(int* per_sm);
 
 // Mask threshold T = floor((d + beta)^2) in coarse voxels (-1: nothing masked).
 int64_t mask_threshold(float d_vox, float beta_vox);

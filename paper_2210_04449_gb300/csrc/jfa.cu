@@ -29,15 +29,22 @@ namespace {
 // (D2, seed) pairs kept in registers: the smallest D2 first, then the
 // smallest seed among the candidates at that D2 -- the same result as a
 // lexicographic (D2, seed) minimum.
-template <bool FINAL>
-__global__ void __launch_bounds__(256) k_jfa_pass(const uint32_t* __restrict__ in,
-                                                 uint32_t* __restrict__ out, int n, int k,
-                                                 float* __restrict__ coarse, float hc, float beta_h) {
-    const int x = blockIdx.x * 32 + threadIdx.x;
-    const int y = blockIdx.y * 8 + threadIdx.y;
+template <bool FINAL, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_jfa_pass(const uint32_t* __restrict__ in,
+                                                     uint32_t* __restrict__ out, int n, int k,
+                                                     float* __restrict__ coarse, float hc, float beta_h) {
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= n || y >= n) return;
     dev::jfa_voxel<FINAL, true>(in, out, n, k, x, y, z, coarse, hc, beta_h);
+}
+
+template <int TX, int TY>
+void launch_pass(rtsdf_ctx* c, const uint32_t* in, uint32_t* out, int n, int k, bool final, float beta_h) {
+    dim3 block(TX, TY, 1), grid((n + TX - 1) / TX, (n + TY - 1) / TY, n);
+    if (final) RTSDF_LAUNCH(c, (k_jfa_pass<true, TX, TY>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
+    else RTSDF_LAUNCH(c, (k_jfa_pass<false, TX, TY>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
 }
 
 // Coarse SDF without a pass (N = 1: no jump steps).
@@ -58,15 +65,16 @@ cudaError_t launch_jfa(rtsdf_ctx* c) {
     int L = 0;
     while ((1 << L) < n) L++;
     const float beta_h = c->cfg.beta_vox * c->hc;
-    dim3 block(32, 8, 1), grid((n + 31) / 32, (n + 7) / 8, n);
     int passes = 0;
     for (int k = L > 0 ? (1 << (L - 1)) : 0; k >= 1; k >>= 1) {
         const uint32_t* in = c->seeds[c->cur];
         uint32_t* out = c->seeds[c->cur ^ 1];
-        if (k == 1)
-            RTSDF_LAUNCH(c, k_jfa_pass<true>, grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
-        else
-            RTSDF_LAUNCH(c, k_jfa_pass<false>, grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
+        switch (c->tune.jfa_tile) {
+            case 1: launch_pass<64, 4>(c, in, out, n, k, k == 1, beta_h); break;
+            case 2: launch_pass<128, 2>(c, in, out, n, k, k == 1, beta_h); break;
+            case 3: launch_pass<32, 4>(c, in, out, n, k, k == 1, beta_h); break;
+            default: launch_pass<32, 8>(c, in, out, n, k, k == 1, beta_h); break;
+        }
         c->cur ^= 1;
         passes++;
     }
@@ -161,9 +169,9 @@ extern "C" rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* se
             const int k = 1 << (L - i);
             uint32_t* out = ((L - i) % 2 == 0) ? seeds_out : scratch;
             if (i == L)
-                k_jfa_pass<true><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
+                k_jfa_pass<true, 32, 8><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
             else
-                k_jfa_pass<false><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
+                k_jfa_pass<false, 32, 8><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
             in = out;
         }
     }

@@ -33,9 +33,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int RAY_CHUNK = 256;   // rays a warp takes from the global counter at a time
-constexpr int REFILL_MIN = 4;    // refill once this many lanes are idle
-
 // Persistent warps: each lane traces one ray at a time and takes a new one
 // as soon as it finishes (from a warp-local chunk of consecutive ray ids, so
 // the lanes of a warp mostly share a texel and its origin).  Finished rays
@@ -64,14 +61,14 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
         while (idle && !exhausted) {
             if (chunk_next == chunk_end) {
                 unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(a.next_ray, (unsigned long long)RAY_CHUNK);
+                if (lane == 0) b = atomicAdd(a.next_ray, (unsigned long long)a.ray_chunk);
                 b = __shfl_sync(0xFFFFFFFFu, b, 0);
                 if (b >= total) {
                     exhausted = true;
                     break;
                 }
                 chunk_next = b;
-                chunk_end = min((uint64_t)b + RAY_CHUNK, total);
+                chunk_end = min((uint64_t)b + (uint64_t)a.ray_chunk, total);
             }
             const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
             const uint32_t want = __popc(idle);
@@ -108,7 +105,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
             }
             const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
             if (act == 0) break;
-            if (!exhausted && (32 - __popc(act)) >= REFILL_MIN) break;
+            if (!exhausted && (32 - __popc(act)) >= a.refill_min) break;
         }
     }
     if (COUNT) {
@@ -134,6 +131,10 @@ __global__ void k_trace_finalize(TraceArgs a) {
 }
 
 }  // namespace
+
+cudaError_t trace_occupancy(int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace<false>, TRACE_THREADS, 0);
+}
 
 cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     TraceArgs a;
@@ -163,13 +164,18 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.ray_min = c->ray_min;
     a.ray_cnt = c->ray_cnt;
     a.next_ray = c->d_next_ray;
+    a.refill_min = c->tune.refill_min;
+    a.ray_chunk = c->tune.ray_chunk;
     cudaError_t e = cudaMemsetAsync(c->d_next_ray, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
-    if (c->trace_grid == 0) {
+    {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, TRACE_THREADS, 0);
-        c->trace_grid = (unsigned)(sms > 0 ? sms : 132) * (unsigned)(per_sm > 0 ? per_sm : 4);
+        if (per_sm < 1) per_sm = 4;
+        const int use = (c->tune.trace_blocks_per_sm > 0 && c->tune.trace_blocks_per_sm < per_sm)
+                            ? c->tune.trace_blocks_per_sm : per_sm;
+        c->trace_grid = (unsigned)(sms > 0 ? sms : 132) * (unsigned)use;
     }
     if (c->counting) RTSDF_LAUNCH(c, k_trace<true>, c->trace_grid, TRACE_THREADS, 0, a);
     else RTSDF_LAUNCH(c, k_trace<false>, c->trace_grid, TRACE_THREADS, 0, a);

@@ -29,6 +29,8 @@ struct TraceArgs {
     uint32_t* ray_min;         // [8 nc^3] per texel slot: min hit distance bits of this frame
     uint32_t* ray_cnt;         // [8 nc^3] per texel slot: front | back << 16 hits of this frame
     unsigned long long* next_ray;
+    int refill_min;            // refill a warp once this many lanes are idle
+    int ray_chunk;             // rays a warp takes from the global counter at a time
 };
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -135,7 +137,7 @@ __device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r
     r.bt = CUDART_INF_F;
     r.bidx = 0x7FFFFFFF;
     r.bfront = false;
-    r.node = a.nt > 1 ? 0 : ~0;
+    r.node = a.nt > 1 ? 0 : (a.nt == 1 ? ~0 : WIDE_EMPTY);   // no triangles: nothing to enter
     r.sp = 0;
     r.slot = slot;
     r.steps = 0;
@@ -174,11 +176,12 @@ struct Stack {
 template <bool COUNT, class A>
 __device__ __forceinline__ bool step_ray(const A& a, Ray& r, Stack& stack, uint32_t& visits, uint32_t& tests) {
     if (COUNT) visits++;
+    const int node = r.node;
+    if (node == WIDE_EMPTY) return true;
     if (++r.steps > 2u * (uint32_t)a.nt + 2u) {   // only a damaged tree gets here
         atomicOr(a.err, ERR_STACK);
         return true;
     }
-    const int node = r.node;
     if (node >= 0) {
         // 4-wide node: test the four child boxes, visit the nearest hit child
         // next and push the others farthest-first with their entry distance
