@@ -349,6 +349,9 @@ def run_batched(dev, frames=3, rays=32, d_vox=2.0):
         for rt in ctxs:
             rt.update(d_vox, rays, f)
     plain_frame(0)
+    for rt in ctxs:
+        rt.set_profiling(True)
+        rt.stats()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -357,6 +360,10 @@ def run_batched(dev, frames=3, rays=32, d_vox=2.0):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain_ms = e0.elapsed_time(e1) / frames
+    plain_stage = {}
+    for rt in ctxs:
+        for k, v in rt.stats()["stage_ms"].items():
+            plain_stage[k] = plain_stage.get(k, 0.0) + v / frames
     ref = [float(rt.grids()["fine"].double().sum().item()) for rt in ctxs]
     for rt in ctxs:
         rt.close()
@@ -377,15 +384,16 @@ def run_batched(dev, frames=3, rays=32, d_vox=2.0):
         b.sync()
         ms.append(b.stats()["last_frame_ms"])
     wall = (time.perf_counter() - t0) * 1e3 / frames
-    got = [float(sc.grids()["fine"].double().sum().item()) for sc in b.scenes]
     info = b.stats()
+    got = [float(sc.grids()["fine"].double().sum().item()) for sc in b.scenes]
     b.close()
     tris = sum(m.nt for m in meshes)
     return {"workload": f"64 scenes, coarse 32..128, {tris:,} tris total, {rays} rays/texel",
             "plain_ms_per_frame": round(plain_ms, 3), "batched_ms_per_frame": round(float(np.mean(ms)), 3),
             "batched_wall_ms_per_frame": round(wall, 3), "speedup": round(plain_ms / float(np.mean(ms)), 3),
             "identical": bool(np.array_equal(np.array(ref), np.array(got))), "graph": bool(info["graph"]),
-            "grid": info["grid"], "tuning": tuned, "launches_per_frame": 1}
+            "grid": info["grid"], "tuning": tuned, "launches_per_frame": 1, "stage_ms": info["stage_ms"],
+            "plain_stage_ms": {k: round(v, 3) for k, v in plain_stage.items() if v > 0}}
 
 
 # ----------------------------------------------------------------- CPU oracle

@@ -229,6 +229,10 @@ typedef struct {
     int32_t graph;          /* 1 when frames replay a captured graph */
     int64_t frames, launches;
     float last_frame_ms;    /* device time of the last frame (CUDA events) */
+    /* stage times of the last frame inside the persistent launch, ms (global
+       timer read at the stage barriers): clear, voxelize, large triangles,
+       jump flood, mask, trace, finalize */
+    float stage_ms[7];
 } rtsdf_batch_info;
 
 /* Creates n scene contexts (1 <= n <= 256) with the given configs.  All

@@ -49,7 +49,7 @@ class Tuning(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_scenes", c_i32), ("grid", c_i32), ("graph", c_i32), ("frames", c_i64), ("launches", c_i64),
-                ("last_frame_ms", c_f)]
+                ("last_frame_ms", c_f), ("stage_ms", c_f * 7)]
 
 
 F3 = c_f * 3

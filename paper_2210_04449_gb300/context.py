@@ -304,7 +304,10 @@ class RTSDFBatch:
     def stats(self) -> dict:
         s = _abi.BatchInfo()
         call("rtsdf_batch_stats", self._h, ctypes.byref(s))
-        return {k: getattr(s, k) for k, _ in _abi.BatchInfo._fields_}
+        out = {k: getattr(s, k) for k, _ in _abi.BatchInfo._fields_ if k != "stage_ms"}
+        names = ("clear", "voxelize", "voxelize_large", "jfa", "mask", "trace", "finalize")
+        out["stage_ms"] = {n: round(float(s.stage_ms[i]), 4) for i, n in enumerate(names)}
+        return out
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

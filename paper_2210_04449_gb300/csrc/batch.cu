@@ -49,6 +49,7 @@ struct SceneDesc {
     float hc, beta_h, beta_vox, alpha;
     int passes;
     int wide_off, tri_off;    // this scene's nodes / leaves in the concatenated BVH
+    uint32_t nmag;            // ceil(2^32 / nc): q = umulhi(v, nmag) = v / nc for v < 2^24
 };
 
 struct BatchParams {
@@ -81,6 +82,7 @@ struct BatchArgs {
     int refill_min;
     int ray_chunk;
     uint32_t spins;
+    unsigned long long* stamps;   // [8] global timer at the stage boundaries (block 0)
     BvhRef bvh;               // every scene's BVH in one array (child ids rebased)
 };
 
@@ -92,6 +94,14 @@ __device__ __forceinline__ int find_scene(const unsigned long long* prefix, int 
         else hi = mid - 1;
     }
     return lo;
+}
+
+__device__ __forceinline__ void stamp(const BatchArgs& b, int k) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        b.stamps[k] = t;
+    }
 }
 
 __device__ bool grid_barrier(const BatchArgs& b) {
@@ -123,26 +133,12 @@ __device__ bool grid_barrier(const BatchArgs& b) {
     return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
-    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t nthr = gridDim.x * (uint64_t)blockDim.x;
-    const BatchParams P = *b.params;
+// Stages 1 and 2 of the batched frame, out of line: the 13-axis overlap
+// setup needs many registers, which would otherwise be reserved across the
+// whole kernel (and spill in the tracer loop).
+__device__ __noinline__ void batch_voxelize_small(const BatchArgs& b, uint64_t tid, uint64_t nthr) {
     const int ns = b.ns;
-    const unsigned long long total_vox = b.vox_prefix[ns], total_tris = b.tri_prefix[ns];
-
-    // ---- stage 0: clear the seed grids and the per-scene counters
-    for (uint64_t g = tid; g < total_vox; g += nthr) {
-        const int s = find_scene(b.vox_prefix, ns, g);
-        b.sc[s].seeds[0][g - b.vox_prefix[s]] = SEED_EMPTY;
-    }
-    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) *const_cast<uint32_t*>(b.sc[s].t.count) = 0u;
-    if (tid == 0) {
-        *b.big_count = 0u;
-        *b.next_ray = 0ull;
-    }
-    if (!grid_barrier(b)) return;
-
-    // ---- stage 1: voxelize (small triangles inline, large ones listed)
+    const unsigned long long total_tris = b.tri_prefix[ns];
     for (uint64_t g = tid; g < total_tris; g += nthr) {
         const int s = find_scene(b.tri_prefix, ns, g);
         const SceneDesc& d = b.sc[s];
@@ -161,9 +157,9 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
                 for (int x = ax.lo[0]; x <= ax.hi[0]; x++)
                     if (overlaps(ax, x, y, z)) d.seeds[0][x + (size_t)n * (y + (size_t)n * z)] = pack_seed(x, y, z);
     }
-    if (!grid_barrier(b)) return;
+}
 
-    // ---- stage 2: large triangles, one block each
+__device__ __noinline__ void batch_voxelize_big(const BatchArgs& b) {
     {
         const uint32_t nb = *(volatile uint32_t*)b.big_count;
         for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
@@ -181,23 +177,63 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nthr = gridDim.x * (uint64_t)blockDim.x;
+    const BatchParams P = *b.params;
+    const int ns = b.ns;
+    stamp(b, 0);
+    // prefix over scenes: voxels in stages 0-4, rays in stages 5-6
+    __shared__ unsigned long long s_prefix[MAX_BATCH + 1];
+    unsigned long long* s_vp = s_prefix;
+    for (int i = threadIdx.x; i <= ns; i += blockDim.x) s_vp[i] = b.vox_prefix[i];
+    __syncthreads();
+
+    // ---- stage 0: clear the seed grids and the per-scene counters
+    for (int s = 0; s < ns; s++) {
+        const uint64_t n3 = s_vp[s + 1] - s_vp[s];
+        uint32_t* sd = b.sc[s].seeds[0];
+        for (uint64_t g = tid; g < n3; g += nthr) sd[g] = SEED_EMPTY;
+    }
+    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) *const_cast<uint32_t*>(b.sc[s].t.count) = 0u;
+    if (tid == 0) {
+        *b.big_count = 0u;
+        *b.next_ray = 0ull;
+    }
     if (!grid_barrier(b)) return;
+    stamp(b, 1);
+
+    // ---- stage 1: voxelize (small triangles inline, large ones listed)
+    batch_voxelize_small(b, tid, nthr);
+    if (!grid_barrier(b)) return;
+    stamp(b, 2);
+
+    // ---- stage 2: large triangles, one block each
+    batch_voxelize_big(b);
+    if (!grid_barrier(b)) return;
+    stamp(b, 3);
 
     // ---- stage 3: jump flooding, pass p of every scene that has one
     for (int p = 0; p < b.max_passes; p++) {
-        for (uint64_t g = tid; g < total_vox; g += nthr) {
-            const int s = find_scene(b.vox_prefix, ns, g);
+        for (int s = 0; s < ns; s++) {
             const SceneDesc& d = b.sc[s];
             const int L = d.passes;
             if (p >= L) continue;
-            const int n = d.t.nc;
-            const uint64_t v = g - b.vox_prefix[s];
-            const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((uint64_t)n * n));
+            const uint32_t n = (uint32_t)d.t.nc, mag = d.nmag, n3 = n * n * n;
+            if (tid >= n3) continue;
             const uint32_t* in = d.seeds[p & 1];
             uint32_t* out = d.seeds[(p + 1) & 1];
             float* coarse = const_cast<float*>(d.t.coarse);
-            if (p == L - 1) jfa_voxel<true, false>(in, out, n, 1 << (L - 1 - p), x, y, z, coarse, d.hc, d.beta_h);
-            else jfa_voxel<false, false>(in, out, n, 1 << (L - 1 - p), x, y, z, coarse, d.hc, d.beta_h);
+            const float hc = d.hc, beta_h = d.beta_h;
+            const int k = 1 << (L - 1 - p);
+            for (uint32_t v = (uint32_t)tid; v < n3; v += (uint32_t)nthr) {
+                const uint32_t vq = __umulhi(v, mag), z = __umulhi(vq, mag);
+                const int x = (int)(v - vq * n), y = (int)(vq - z * n);
+                if (p == L - 1) jfa_voxel<true, false>(in, out, (int)n, k, x, y, (int)z, coarse, hc, beta_h);
+                else jfa_voxel<false, false>(in, out, (int)n, k, x, y, (int)z, coarse, hc, beta_h);
+            }
         }
         if (!grid_barrier(b)) return;
     }
@@ -210,71 +246,84 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
         }
     }
     if (!grid_barrier(b)) return;
+    stamp(b, 4);
 
     // ---- stage 4: near-surface mask, fill, Eq. 1 decay (static scenes: no reset)
     {
         const unsigned lane = threadIdx.x & 31;
-        const uint64_t warp0 = tid - lane;
-        for (uint64_t base = warp0; base < total_vox; base += nthr) {
-            const uint64_t g = base + lane;
-            const bool valid = g < total_vox;
-            int s = 0;
-            bool masked = false;
-            uint64_t v = 0;
-            if (valid) {
-                s = find_scene(b.vox_prefix, ns, g);
-                const SceneDesc& d = b.sc[s];
-                const int n = d.t.nc;
-                v = g - b.vox_prefix[s];
-                const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((uint64_t)n * n));
-                const uint32_t sv = d.seeds[d.passes & 1][v];
-                const double sd = (double)P.d_vox + (double)d.beta_vox;
-                const long long T = sd < 0 ? -1 : (long long)floor(sd * sd);
-                if (sv != SEED_EMPTY) {
-                    const int dx = (int)(sv & 0xFF) - x, dy = (int)((sv >> 8) & 0xFF) - y, dz = (int)((sv >> 16) & 0xFF) - z;
-                    masked = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz <= T;
-                }
-                const float c = d.t.coarse[v];
-                const int nf = 2 * n;
-                for (int cz = 0; cz < 2; cz++)
-                    for (int cy = 0; cy < 2; cy++)
-                        for (int cxx = 0; cxx < 2; cxx++) {
-                            const size_t j = (size_t)(2 * x + cxx) + (size_t)nf * ((size_t)(2 * y + cy) + (size_t)nf * (2 * z + cz));
-                            const float u = d.t.accum[j];
-                            if (!masked) {
-                                d.t.fine[j] = c;
-                                if (u != CUDART_INF_F) {
-                                    d.t.accum[j] = CUDART_INF_F;
-                                    d.t.counts[j] = 0u;
+        const uint32_t warp0 = (uint32_t)(tid - lane);
+        for (int s = 0; s < ns; s++) {
+            const SceneDesc& dg = b.sc[s];
+            const uint32_t n = (uint32_t)dg.t.nc, mag = dg.nmag, n3 = n * n * n;
+            if (warp0 >= n3) continue;
+            // local copies: stores through the grid pointers below could
+            // otherwise alias the descriptor and force reloads
+            const uint32_t* seeds_fin = dg.seeds[dg.passes & 1];
+            const float* coarse = dg.t.coarse;
+            float* accum = dg.t.accum;
+            uint32_t* counts = dg.t.counts;
+            float* fine = dg.t.fine;
+            uint32_t* list = const_cast<uint32_t*>(dg.t.masked);
+            uint32_t* count = const_cast<uint32_t*>(dg.t.count);
+            const float alpha = dg.alpha;
+            const double sdv = (double)P.d_vox + (double)dg.beta_vox;
+            const long long T = sdv < 0 ? -1 : (long long)floor(sdv * sdv);
+            const uint32_t nf = 2 * n;
+            for (uint32_t base = warp0; base < n3; base += (uint32_t)nthr) {
+                const uint32_t v = base + lane;
+                const bool valid = v < n3;
+                bool masked = false;
+                if (valid) {
+                    const uint32_t vq = __umulhi(v, mag), z = __umulhi(vq, mag);
+                    const int x = (int)(v - vq * n), y = (int)(vq - z * n);
+                    const uint32_t sv = seeds_fin[v];
+                    if (sv != SEED_EMPTY) {
+                        const int dx = (int)(sv & 0xFF) - x, dy = (int)((sv >> 8) & 0xFF) - y;
+                        const int dz = (int)((sv >> 16) & 0xFF) - (int)z;
+                        masked = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz <= T;
+                    }
+                    const float c = coarse[v];
+                    for (int cz = 0; cz < 2; cz++)
+                        for (int cy = 0; cy < 2; cy++)
+                            for (int cx = 0; cx < 2; cx++) {
+                                const size_t j = (size_t)(2 * x + cx) +
+                                                 (size_t)nf * ((size_t)(2 * y + cy) + (size_t)nf * (2 * z + cz));
+                                const float u = accum[j];
+                                if (!masked) {
+                                    fine[j] = c;
+                                    if (u != CUDART_INF_F) {
+                                        accum[j] = CUDART_INF_F;
+                                        counts[j] = 0u;
+                                    }
+                                } else if (alpha != 1.f) {
+                                    float un = u;
+                                    if (alpha == 0.f) un = c;
+                                    else if (u != CUDART_INF_F)
+                                        un = __fadd_rn(__fmul_rn(alpha, u), __fmul_rn(1.f - alpha, c));
+                                    if (un != u) accum[j] = un;
                                 }
-                            } else if (d.alpha != 1.f) {
-                                float un = u;
-                                if (d.alpha == 0.f) un = c;
-                                else if (u != CUDART_INF_F)
-                                    un = __fadd_rn(__fmul_rn(d.alpha, u), __fmul_rn(1.f - d.alpha, c));
-                                if (un != u) d.t.accum[j] = un;
                             }
-                        }
-            }
-            // warp-aggregated append per scene
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, masked);
-            if (masked) {
-                const unsigned peers = __match_any_sync(bal, s);
-                const int leader = __ffs(peers) - 1;
-                uint32_t base_slot = 0;
-                if ((int)lane == leader)
-                    base_slot = atomicAdd(const_cast<uint32_t*>(b.sc[s].t.count), (uint32_t)__popc(peers));
-                base_slot = __shfl_sync(peers, base_slot, leader);
-                const_cast<uint32_t*>(b.sc[s].t.masked)[base_slot + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)v;
+                }
+                // warp-aggregated append
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, masked);
+                if (bal) {
+                    const int leader = __ffs(bal) - 1;
+                    uint32_t slot0 = 0;
+                    if ((int)lane == leader) slot0 = atomicAdd(count, (uint32_t)__popc(bal));
+                    slot0 = __shfl_sync(0xFFFFFFFFu, slot0, leader);
+                    if (masked) list[slot0 + __popc(bal & ((1u << lane) - 1u))] = v;
+                }
             }
         }
     }
     if (!grid_barrier(b)) return;
+    stamp(b, 5);
 
     // ---- stage 5: trace all scenes' rays with dynamic fetch
-    __shared__ unsigned long long s_rp[MAX_BATCH + 1];   // ray prefix over scenes
+    unsigned long long* s_rp = s_prefix;
     __shared__ int s_id[SMEM_STACK][TRACE_THREADS];
     __shared__ float s_t[SMEM_STACK][TRACE_THREADS];
+    __syncthreads();   // every thread is done with the voxel prefix
     if (threadIdx.x == 0) {
         unsigned long long acc = 0;
         for (int s = 0; s < ns; s++) {
@@ -293,7 +342,8 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
         Ray r;
         int scene = 0;
         bool active = false;
-        unsigned long long chunk_next = 0, chunk_end = 0;
+        unsigned long long chunk_next = 0, chunk_end = 0, chunk_scene_end = 0;
+        int chunk_scene = 0;
         bool exhausted = false;
         uint32_t dummy_v = 0, dummy_t = 0;
         for (;;) {
@@ -309,6 +359,11 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
                     }
                     chunk_next = c0;
                     chunk_end = min(c0 + (unsigned long long)b.ray_chunk, total);
+                    // scene of the chunk's first ray and where that scene ends
+                    int cs = 0;
+                    if (lane == 0) cs = find_scene(s_rp, ns, c0);
+                    chunk_scene = __shfl_sync(0xFFFFFFFFu, cs, 0);
+                    chunk_scene_end = s_rp[chunk_scene + 1];
                 }
                 const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
                 const uint32_t want = __popc(idle);
@@ -317,7 +372,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
                     const uint32_t rank = __popc(idle & lt);
                     if (rank < take) {
                         const unsigned long long g = chunk_next + rank;
-                        scene = find_scene(s_rp, ns, g);
+                        scene = g < chunk_scene_end ? chunk_scene : find_scene(s_rp, ns, g);
                         TraceArgs ta = b.sc[scene].t;
                         ta.rays = P.rays;
                         ta.log2_rays = P.log2_rays;
@@ -358,17 +413,17 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
         }
     }
     if (!grid_barrier(b)) return;
+    stamp(b, 6);
 
-    // ---- stage 6: Eq. 1 finalize of every traced texel slot
-    {
-        unsigned long long total_slots = 0;
-        for (int s = 0; s < ns; s++) total_slots += (unsigned long long)(*(volatile const uint32_t*)b.sc[s].t.count) * 8ull;
-        for (uint64_t g = tid; g < total_slots; g += nthr) {
-            // slot prefix = ray prefix / rays
-            const int s = find_scene(s_rp, ns, g * (unsigned long long)P.rays);
-            finalize_slot(b.sc[s].t, g - s_rp[s] / (unsigned long long)P.rays);
-        }
+    // ---- stage 6: Eq. 1 finalize of every traced texel slot, scene by scene
+    for (int s = 0; s < ns; s++) {
+        const unsigned long long slots = (s_rp[s + 1] - s_rp[s]) >> P.log2_rays;
+        if (tid >= slots) continue;
+        const TraceArgs ta = b.sc[s].t;
+        for (uint64_t g = tid; g < slots; g += nthr) finalize_slot(ta, g);
     }
+    grid_barrier(b);
+    stamp(b, 7);
 }
 
 // Copy one scene's 4-wide nodes into the concatenated array, rebasing child
@@ -405,6 +460,7 @@ struct rtsdf_batch {
     float4* d_tri_all = nullptr;     // all scenes' leaf triangles
     int64_t wide_cap = 0, tri_cap = 0, total_nt = 0;
     uint32_t* d_ctr = nullptr;   // big_count, bar_count, bar_gen, abort, err
+    unsigned long long* d_stamps = nullptr;
     unsigned long long* d_next_ray = nullptr;
     BatchParams* d_params = nullptr;
     BatchParams* h_params = nullptr;   // pinned
@@ -488,6 +544,7 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
         int L = 0;
         while ((1 << L) < c->nc) L++;
         d.passes = L;
+        d.nmag = (uint32_t)((0x100000000ull + (unsigned long long)c->nc - 1) / (unsigned long long)c->nc);
         maxp = L > maxp ? L : maxp;
         vp[s] = av;
         tp[s] = at;
@@ -577,6 +634,7 @@ cudaError_t launch_frame_kernel(rtsdf_batch* b) {
     a.refill_min = b->refill_min;
     a.ray_chunk = b->ray_chunk;
     a.spins = b->barrier_spins > 0 ? (uint32_t)b->barrier_spins : BARRIER_SPINS;
+    a.stamps = b->d_stamps;
     a.bvh.wide = b->d_wide_all;
     a.bvh.tri = b->d_tri_all;
     a.bvh.nt = b->total_nt;
@@ -634,6 +692,8 @@ rtsdf_status rtsdf_batch_create(const rtsdf_config* cfgs, int32_t n, rtsdf_batch
         if (!e) e = cudaMalloc(&b->d_ctr, sizeof(uint32_t) * 8);
         if (!e) e = cudaMemset(b->d_ctr, 0, sizeof(uint32_t) * 8);
         if (!e) e = cudaMalloc(&b->d_next_ray, sizeof(unsigned long long));
+        if (!e) e = cudaMalloc(&b->d_stamps, sizeof(unsigned long long) * 8);
+        if (!e) e = cudaMemset(b->d_stamps, 0, sizeof(unsigned long long) * 8);
         if (!e) e = cudaMalloc(&b->d_params, sizeof(BatchParams));
         if (!e) e = cudaMallocHost(&b->h_params, sizeof(BatchParams));
         if (!e) e = cudaEventCreate(&b->ev0);
@@ -661,6 +721,7 @@ rtsdf_status rtsdf_batch_destroy(rtsdf_batch_t b) {
     if (b->d_tri_all) cudaFree(b->d_tri_all);
     if (b->d_ctr) cudaFree(b->d_ctr);
     if (b->d_next_ray) cudaFree(b->d_next_ray);
+    if (b->d_stamps) cudaFree(b->d_stamps);
     if (b->d_params) cudaFree(b->d_params);
     if (b->h_params) cudaFreeHost(b->h_params);
     if (b->ev0) cudaEventDestroy(b->ev0);
@@ -802,6 +863,9 @@ rtsdf_status rtsdf_batch_stats(rtsdf_batch_t b, rtsdf_batch_info* out) {
     float ms = -1.f;
     if (b->frames > 0 && cudaEventElapsedTime(&ms, b->ev0, b->ev1) != cudaSuccess) ms = -1.f;
     out->last_frame_ms = ms;
+    unsigned long long st[8];
+    if (cudaMemcpy(st, b->d_stamps, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess)
+        for (int k = 0; k < 7; k++) out->stage_ms[k] = st[k + 1] >= st[k] ? (float)((st[k + 1] - st[k]) * 1e-6) : 0.f;
     return RTSDF_OK;
 }
 
@@ -881,11 +945,11 @@ extern "C" rtsdf_status rtsdf_batch_autotune(rtsdf_batch_t b, float d_vox, int32
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (!e) e = snap.take(b);
     if (e) return from_cuda_b(e);
-    // one warm frame (graph capture) and one timed frame per candidate, both
-    // from the saved state
+    // one timed frame per candidate from the saved state (the events bracket
+    // only the replay, not the graph capture)
     auto trial = [&](const rtsdf_batch_tuning& t, float* ms) -> rtsdf_status {
         rtsdf_status s = rtsdf_batch_set_tuning(b, &t);
-        for (int rep = 0; rep < 2 && s == RTSDF_OK; rep++) {
+        if (s == RTSDF_OK) {
             cudaError_t r = snap.restore(b);
             if (r) return from_cuda_b(r);
             s = rtsdf_batch_frame(b, d_vox, rays, frame);

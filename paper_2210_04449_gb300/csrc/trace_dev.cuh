@@ -186,24 +186,28 @@ __device__ __forceinline__ bool step_ray(const A& a, Ray& r, Stack& stack, uint3
         // 4-wide node: test the four child boxes, visit the nearest hit child
         // next and push the others farthest-first with their entry distance
         const WNode* w = a.wide + node;
-        const float4 lx = __ldg(&w->lox), hx = __ldg(&w->hix);
-        const float4 ly = __ldg(&w->loy), hy = __ldg(&w->hiy);
-        const float4 lz = __ldg(&w->loz), hz = __ldg(&w->hiz);
+        // near / far plane rows chosen by the ray's direction signs (rows:
+        // lox, hix, loy, hiy, loz, hiz), so each slab needs no min/max of its
+        // two planes; an empty slot (lo = +inf, hi = -inf) never hits
+        const float4* row = &w->lox;
+        const int sx = r.id.x < 0.f, sy = r.id.y < 0.f, sz = r.id.z < 0.f;
+        const float4 nx = __ldg(row + sx), fx = __ldg(row + 1 - sx);
+        const float4 ny = __ldg(row + 2 + sy), fy = __ldg(row + 3 - sy);
+        const float4 nz = __ldg(row + 4 + sz), fz = __ldg(row + 5 - sz);
         const int4 ch = __ldg(&w->child);
         float key[4];
         int val[4] = {ch.x, ch.y, ch.z, ch.w};
-        const float blx[4] = {lx.x, lx.y, lx.z, lx.w}, bhx[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float bly[4] = {ly.x, ly.y, ly.z, ly.w}, bhy[4] = {hy.x, hy.y, hy.z, hy.w};
-        const float blz[4] = {lz.x, lz.y, lz.z, lz.w}, bhz[4] = {hz.x, hz.y, hz.z, hz.w};
+        const float bnx[4] = {nx.x, nx.y, nx.z, nx.w}, bfx[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float bny[4] = {ny.x, ny.y, ny.z, ny.w}, bfy[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float bnz[4] = {nz.x, nz.y, nz.z, nz.w}, bfz[4] = {fz.x, fz.y, fz.z, fz.w};
         int nh = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const float x0 = fmaf(blx[k], r.id.x, -r.oid.x), x1 = fmaf(bhx[k], r.id.x, -r.oid.x);
-            const float y0 = fmaf(bly[k], r.id.y, -r.oid.y), y1 = fmaf(bhy[k], r.id.y, -r.oid.y);
-            const float z0 = fmaf(blz[k], r.id.z, -r.oid.z), z1 = fmaf(bhz[k], r.id.z, -r.oid.z);
-            const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.f));
-            const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), r.bt));
-            const bool hit = t0 <= t1 && val[k] != WIDE_EMPTY;
+            const float t0 = fmaxf(fmaxf(fmaf(bnx[k], r.id.x, -r.oid.x), fmaf(bny[k], r.id.y, -r.oid.y)),
+                                   fmaxf(fmaf(bnz[k], r.id.z, -r.oid.z), 0.f));
+            const float t1 = fminf(fminf(fmaf(bfx[k], r.id.x, -r.oid.x), fmaf(bfy[k], r.id.y, -r.oid.y)),
+                                   fminf(fmaf(bfz[k], r.id.z, -r.oid.z), r.bt));
+            const bool hit = t0 <= t1;
             key[k] = hit ? t0 : CUDART_INF_F;
             nh += hit;
         }
