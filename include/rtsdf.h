@@ -221,6 +221,7 @@ typedef struct {
     int32_t use_graph;      /* replay the frame from a CUDA graph (1) or launch directly (0) */
     int32_t barrier_spins;  /* polls before a grid-barrier wait gives up with RTSDF_E_TIMEOUT
                                (0 = default, about ten seconds) */
+    int32_t leaf_min;       /* tracer: run the leaf phase once this many lanes hold a parked leaf */
 } rtsdf_batch_tuning;
 
 typedef struct {
@@ -260,6 +261,7 @@ typedef struct {
     int32_t trace_blocks_per_sm; /* persistent tracer blocks per SM (0 = occupancy maximum) */
     int32_t refill_min;          /* tracer: refill a warp once this many lanes are idle (1..32) */
     int32_t ray_chunk;           /* tracer: rays a warp takes from the global counter at a time */
+    int32_t leaf_min;            /* tracer: run the leaf phase once this many lanes hold a parked leaf (1..32) */
 } rtsdf_tuning;
 
 rtsdf_status rtsdf_set_tuning(rtsdf_t ctx, const rtsdf_tuning* t);

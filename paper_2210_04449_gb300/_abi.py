@@ -40,11 +40,12 @@ class Stats(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", c_i32), ("refill_min", c_i32), ("ray_chunk", c_i32), ("use_graph", c_i32),
-                ("barrier_spins", c_i32)]
+                ("barrier_spins", c_i32), ("leaf_min", c_i32)]
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("jfa_tile", c_i32), ("trace_blocks_per_sm", c_i32), ("refill_min", c_i32), ("ray_chunk", c_i32)]
+    _fields_ = [("jfa_tile", c_i32), ("trace_blocks_per_sm", c_i32), ("refill_min", c_i32), ("ray_chunk", c_i32),
+                ("leaf_min", c_i32)]
 
 
 class BatchInfo(ctypes.Structure):

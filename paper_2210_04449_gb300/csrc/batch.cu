@@ -81,6 +81,7 @@ struct BatchArgs {
     uint32_t* err;
     int refill_min;
     int ray_chunk;
+    int leaf_min;
     uint32_t spins;
     unsigned long long* stamps;   // [8] global timer at the stage boundaries (block 0)
     BvhRef bvh;               // every scene's BVH in one array (child ids rebased)
@@ -389,8 +390,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
             }
             if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
             for (;;) {
-                bool done = false;
-                if (active) done = step_ray<false>(b.bvh, r, stk, dummy_v, dummy_t);
+                const bool done = warp_step<false>(b.bvh, r, stk, active, b.leaf_min, dummy_v, dummy_t);
                 const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
                 if (fin && done) {
                     const unsigned long long key = ((unsigned long long)scene << 32) | r.slot;
@@ -468,8 +468,9 @@ struct rtsdf_batch {
     int max_passes = 0;
     // launch configuration (autotuned)
     int blocks_per_sm = 0;       // 0 = occupancy maximum
-    int refill_min = 4;
-    int ray_chunk = 256;
+    int refill_min = 16;
+    int ray_chunk = 1024;
+    int leaf_min = 16;
     int use_graph = 1;
     int barrier_spins = 0;
     unsigned grid = 0;
@@ -545,6 +546,7 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
         while ((1 << L) < c->nc) L++;
         d.passes = L;
         d.nmag = (uint32_t)((0x100000000ull + (unsigned long long)c->nc - 1) / (unsigned long long)c->nc);
+        d.t.nc_mag = d.nmag;
         maxp = L > maxp ? L : maxp;
         vp[s] = av;
         tp[s] = at;
@@ -633,6 +635,7 @@ cudaError_t launch_frame_kernel(rtsdf_batch* b) {
     a.next_ray = b->d_next_ray;
     a.refill_min = b->refill_min;
     a.ray_chunk = b->ray_chunk;
+    a.leaf_min = b->leaf_min;
     a.spins = b->barrier_spins > 0 ? (uint32_t)b->barrier_spins : BARRIER_SPINS;
     a.stamps = b->d_stamps;
     a.bvh.wide = b->d_wide_all;
@@ -742,10 +745,11 @@ rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_t b, const rtsdf_batch_tuning* t
     if (t->blocks_per_sm < 0 || t->refill_min < 1 || t->refill_min > 32 || t->ray_chunk < 32 ||
         t->ray_chunk > (1 << 20))
         return RTSDF_E_ARG;
-    if (t->barrier_spins < 0) return RTSDF_E_ARG;
+    if (t->barrier_spins < 0 || t->leaf_min < 1 || t->leaf_min > 32) return RTSDF_E_ARG;
     if (t->blocks_per_sm != b->blocks_per_sm || t->refill_min != b->refill_min || t->ray_chunk != b->ray_chunk ||
-        t->use_graph != b->use_graph || t->barrier_spins != b->barrier_spins)
+        t->use_graph != b->use_graph || t->barrier_spins != b->barrier_spins || t->leaf_min != b->leaf_min)
         drop_graph(b);
+    b->leaf_min = t->leaf_min;
     b->barrier_spins = t->barrier_spins;
     b->blocks_per_sm = t->blocks_per_sm;
     b->refill_min = t->refill_min;
@@ -761,6 +765,7 @@ rtsdf_status rtsdf_batch_get_tuning(rtsdf_batch_t b, rtsdf_batch_tuning* t) {
     t->ray_chunk = b->ray_chunk;
     t->use_graph = b->use_graph;
     t->barrier_spins = b->barrier_spins;
+    t->leaf_min = b->leaf_min;
     return RTSDF_OK;
 }
 
@@ -968,6 +973,18 @@ extern "C" rtsdf_status rtsdf_batch_autotune(rtsdf_batch_t b, float d_vox, int32
         if (st != RTSDF_OK || r == cur.refill_min) continue;
         rtsdf_batch_tuning t = cur;
         t.refill_min = r;
+        float ms = 0.f;
+        st = trial(t, &ms);
+        if (st == RTSDF_OK && ms < base) {
+            base = ms;
+            cur = t;
+        }
+    }
+    const int leafs[] = {8, 16, 24};
+    for (int lm : leafs) {
+        if (st != RTSDF_OK || lm == cur.leaf_min) continue;
+        rtsdf_batch_tuning t = cur;
+        t.leaf_min = lm;
         float ms = 0.f;
         st = trial(t, &ms);
         if (st == RTSDF_OK && ms < base) {

@@ -141,7 +141,7 @@ struct rtsdf_ctx {
     unsigned trace_grid = 0;
 
     // launch parameters (rtsdf_set_tuning / rtsdf_autotune)
-    rtsdf_tuning tune = {0, 0, 4, 256};
+    rtsdf_tuning tune = {0, 0, 16, 1024, 16};
 
     rtsdf::Bvh bvh;
     bool bvh_dirty = true;

@@ -87,8 +87,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         // trace until enough lanes are idle to be worth a refill
         for (;;) {
-            bool done = false;
-            if (active) done = step_ray<COUNT>(a, r, stk, n_visits, n_tests);
+            const bool done = warp_step<COUNT>(a, r, stk, active, a.leaf_min, n_visits, n_tests);
             const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
             if (fin && done) {
                 const unsigned peers = __match_any_sync(fin, r.slot);
@@ -166,6 +165,8 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.next_ray = c->d_next_ray;
     a.refill_min = c->tune.refill_min;
     a.ray_chunk = c->tune.ray_chunk;
+    a.leaf_min = c->tune.leaf_min;
+    a.nc_mag = (uint32_t)((0x100000000ull + (unsigned long long)c->nc - 1) / (unsigned long long)c->nc);
     cudaError_t e = cudaMemsetAsync(c->d_next_ray, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     {

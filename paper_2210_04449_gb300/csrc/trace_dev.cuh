@@ -31,6 +31,8 @@ struct TraceArgs {
     unsigned long long* next_ray;
     int refill_min;            // refill a warp once this many lanes are idle
     int ray_chunk;             // rays a warp takes from the global counter at a time
+    int leaf_min;              // run the leaf phase once this many lanes hold a parked leaf
+    uint32_t nc_mag;           // ceil(2^32 / nc): umulhi(v, nc_mag) = v / nc for v < 2^24
 };
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -103,8 +105,11 @@ __device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 v0, float3 e1
     return true;
 }
 
+// Reciprocal of a direction component for the box tests only (an
+// approximate reciprocal is enough: the same value serves every box of the
+// ray and the leaf boxes are padded); zero components become +-1e30.
 __device__ __forceinline__ float safe_inv(float d) {
-    return __fdiv_rn(1.0f, fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
+    return __fdividef(1.0f, fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
 }
 
 // Per-lane ray state of the persistent tracer.
@@ -113,7 +118,8 @@ struct Ray {
     float bt;          // closest hit distance so far
     int bidx;          // its original triangle index (0x7FFFFFFF: none)
     bool bfront;
-    int node;          // next node to enter (>= 0 internal, < 0 ~leaf)
+    int node;          // next node to enter (>= 0 internal, < 0 ~leaf, WIDE_EMPTY none)
+    int leaf;          // parked leaf waiting for the leaf phase (WIDE_EMPTY none)
     int sp;
     uint32_t slot;     // texel slot = 8 * (masked-list position) + child
     uint32_t steps;    // nodes entered; a tree of 2 nt - 1 nodes bounds it
@@ -125,7 +131,8 @@ __device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r
     const uint32_t parent = a.masked[slot >> 3];
     const uint32_t ch = slot & 7u;
     const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
-    const uint32_t px = parent % nc, py = (parent / nc) % nc, pz = parent / (nc * nc);
+    const uint32_t pq = __umulhi(parent, a.nc_mag), pz = __umulhi(pq, a.nc_mag);
+    const uint32_t px = parent - pq * nc, py = pq - pz * nc;
     const uint32_t jx = 2 * px + (ch & 1), jy = 2 * py + ((ch >> 1) & 1), jz = 2 * pz + (ch >> 2);
     const uint32_t texel = jx + nf * (jy + nf * jz);
     r.o = make_float3(__fadd_rn(a.bx, __fmul_rn(__fadd_rn((float)jx, 0.5f), a.hf)),
@@ -138,13 +145,12 @@ __device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r
     r.bidx = 0x7FFFFFFF;
     r.bfront = false;
     r.node = a.nt > 1 ? 0 : (a.nt == 1 ? ~0 : WIDE_EMPTY);   // no triangles: nothing to enter
+    r.leaf = WIDE_EMPTY;
     r.sp = 0;
     r.slot = slot;
     r.steps = 0;
 }
 
-// One traversal step (enter one node or test one leaf).  Returns true when
-// the ray's traversal is complete.
 constexpr int TRACE_THREADS = 128;
 constexpr int SMEM_STACK = 24;
 
@@ -172,93 +178,147 @@ struct Stack {
     }
 };
 
-// A: any argument block with the BVH fields wide, tri, nt and err.
+
+// Traversal in two phases.  With one triangle per leaf, a warp in which
+// every lane takes either a node step or a leaf step would pay both paths on
+// almost every iteration.  So a lane that reaches a leaf parks it (one per
+// lane) and keeps entering internal nodes; the warp runs the leaf phase only
+// when enough lanes hold a parked leaf or some cannot continue.  The order of
+// triangle tests does not change the closest hit (every triangle whose box
+// the ray meets is tested unless its entry distance exceeds the best hit).
+
+// next stack entry that can still hold a hit at distance <= bt (WIDE_EMPTY: none)
+__device__ __forceinline__ int pop_next(Ray& r, Stack& stack) {
+    while (r.sp > 0) {
+        int nx;
+        float te;
+        stack.pop(--r.sp, nx, te);
+        if (te <= r.bt) return nx;
+    }
+    return WIDE_EMPTY;
+}
+
+// while the next node is a leaf and no leaf is parked, park it and go on
+// with the next stack entry
+__device__ __forceinline__ void park_leaves(Ray& r, Stack& stack) {
+    while (r.node != WIDE_EMPTY && r.node < 0 && r.leaf == WIDE_EMPTY) {
+        r.leaf = ~r.node;
+        r.node = pop_next(r, stack);
+    }
+}
+
+__device__ __forceinline__ bool ray_done(const Ray& r) { return r.node == WIDE_EMPTY && r.leaf == WIDE_EMPTY; }
+
+// Enter r.node if it is an internal node (A: any argument block with the BVH
+// fields wide, tri, nt and err).
 template <bool COUNT, class A>
-__device__ __forceinline__ bool step_ray(const A& a, Ray& r, Stack& stack, uint32_t& visits, uint32_t& tests) {
-    if (COUNT) visits++;
+__device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint32_t& visits) {
     const int node = r.node;
-    if (node == WIDE_EMPTY) return true;
+    if (node < 0) return;   // none, or a leaf waiting behind the parked one
     if (++r.steps > 2u * (uint32_t)a.nt + 2u) {   // only a damaged tree gets here
         atomicOr(a.err, ERR_STACK);
-        return true;
+        r.node = r.leaf = WIDE_EMPTY;
+        return;
     }
-    if (node >= 0) {
-        // 4-wide node: test the four child boxes, visit the nearest hit child
-        // next and push the others farthest-first with their entry distance
-        const WNode* w = a.wide + node;
-        // near / far plane rows chosen by the ray's direction signs (rows:
-        // lox, hix, loy, hiy, loz, hiz), so each slab needs no min/max of its
-        // two planes; an empty slot (lo = +inf, hi = -inf) never hits
-        const float4* row = &w->lox;
-        const int sx = r.id.x < 0.f, sy = r.id.y < 0.f, sz = r.id.z < 0.f;
-        const float4 nx = __ldg(row + sx), fx = __ldg(row + 1 - sx);
-        const float4 ny = __ldg(row + 2 + sy), fy = __ldg(row + 3 - sy);
-        const float4 nz = __ldg(row + 4 + sz), fz = __ldg(row + 5 - sz);
-        const int4 ch = __ldg(&w->child);
-        float key[4];
-        int val[4] = {ch.x, ch.y, ch.z, ch.w};
-        const float bnx[4] = {nx.x, nx.y, nx.z, nx.w}, bfx[4] = {fx.x, fx.y, fx.z, fx.w};
-        const float bny[4] = {ny.x, ny.y, ny.z, ny.w}, bfy[4] = {fy.x, fy.y, fy.z, fy.w};
-        const float bnz[4] = {nz.x, nz.y, nz.z, nz.w}, bfz[4] = {fz.x, fz.y, fz.z, fz.w};
-        int nh = 0;
+    if (COUNT) visits++;
+    // 4-wide node: test the four child boxes, visit the nearest hit child
+    // next and push the others farthest-first with their entry distance.
+    // Near / far plane rows are chosen by the ray's direction signs (rows:
+    // lox, hix, loy, hiy, loz, hiz), so each slab needs no min/max of its two
+    // planes; an empty slot (lo = +inf, hi = -inf) never hits.
+    const WNode* w = a.wide + node;
+    const float4* row = &w->lox;
+    const int sx = r.id.x < 0.f, sy = r.id.y < 0.f, sz = r.id.z < 0.f;
+    const float4 nx = __ldg(row + sx), fx = __ldg(row + 1 - sx);
+    const float4 ny = __ldg(row + 2 + sy), fy = __ldg(row + 3 - sy);
+    const float4 nz = __ldg(row + 4 + sz), fz = __ldg(row + 5 - sz);
+    const int4 ch = __ldg(&w->child);
+    float key[4];
+    int val[4] = {ch.x, ch.y, ch.z, ch.w};
+    const float bnx[4] = {nx.x, nx.y, nx.z, nx.w}, bfx[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float bny[4] = {ny.x, ny.y, ny.z, ny.w}, bfy[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float bnz[4] = {nz.x, nz.y, nz.z, nz.w}, bfz[4] = {fz.x, fz.y, fz.z, fz.w};
+    int nh = 0;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float t0 = fmaxf(fmaxf(fmaf(bnx[k], r.id.x, -r.oid.x), fmaf(bny[k], r.id.y, -r.oid.y)),
-                                   fmaxf(fmaf(bnz[k], r.id.z, -r.oid.z), 0.f));
-            const float t1 = fminf(fminf(fmaf(bfx[k], r.id.x, -r.oid.x), fmaf(bfy[k], r.id.y, -r.oid.y)),
-                                   fminf(fmaf(bfz[k], r.id.z, -r.oid.z), r.bt));
-            const bool hit = t0 <= t1;
-            key[k] = hit ? t0 : CUDART_INF_F;
-            nh += hit;
-        }
-        if (nh > 0) {
-            // ascending sort of (key, val): a 5-exchange network
+    for (int k = 0; k < 4; k++) {
+        const float t0 = fmaxf(fmaxf(fmaf(bnx[k], r.id.x, -r.oid.x), fmaf(bny[k], r.id.y, -r.oid.y)),
+                               fmaxf(fmaf(bnz[k], r.id.z, -r.oid.z), 0.f));
+        const float t1 = fminf(fminf(fmaf(bfx[k], r.id.x, -r.oid.x), fmaf(bfy[k], r.id.y, -r.oid.y)),
+                               fminf(fmaf(bfz[k], r.id.z, -r.oid.z), r.bt));
+        const bool hit = t0 <= t1;
+        key[k] = hit ? t0 : CUDART_INF_F;
+        nh += hit;
+    }
+    if (nh > 0) {
+        // ascending sort of (key, val): a 5-exchange network
 #define RTSDF_CAS(i, j)                                                     \
     if (key[j] < key[i]) {                                                  \
         const float tk = key[i]; key[i] = key[j]; key[j] = tk;              \
         const int tv = val[i]; val[i] = val[j]; val[j] = tv;                \
     }
-            RTSDF_CAS(0, 1) RTSDF_CAS(2, 3) RTSDF_CAS(0, 2) RTSDF_CAS(1, 3) RTSDF_CAS(1, 2)
+        RTSDF_CAS(0, 1) RTSDF_CAS(2, 3) RTSDF_CAS(0, 2) RTSDF_CAS(1, 3) RTSDF_CAS(1, 2)
 #undef RTSDF_CAS
 #pragma unroll
-            for (int k = 3; k >= 1; k--) {
-                if (k < nh) {
-                    if (r.sp < TRACE_STACK) stack.push(r.sp++, val[k], key[k]);
-                    else atomicOr(a.err, ERR_STACK);
-                }
+        for (int k = 3; k >= 1; k--) {
+            if (k < nh) {
+                if (r.sp < TRACE_STACK) stack.push(r.sp++, val[k], key[k]);
+                else atomicOr(a.err, ERR_STACK);
             }
-            r.node = val[0];
-            return false;
         }
+        r.node = val[0];
     } else {
-        if (COUNT) tests++;
-        const int leaf = ~node;
-        const float4 p0 = __ldg(&a.tri[3 * leaf]);
-        const float4 p1 = __ldg(&a.tri[3 * leaf + 1]);
-        const float4 p2 = __ldg(&a.tri[3 * leaf + 2]);
-        float t;
-        bool fr;
-        if (ray_tri(r.o, r.d, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
-                    make_float3(p2.x, p2.y, p2.z), t, fr)) {
-            const int idx = __float_as_int(p0.w);
-            if (t < r.bt || (t == r.bt && idx < r.bidx)) {
-                r.bt = t;
-                r.bidx = idx;
-                r.bfront = fr;
-            }
+        r.node = pop_next(r, stack);
+    }
+    park_leaves(r, stack);
+}
+
+// Test the parked leaf, if any.
+template <bool COUNT, class A>
+__device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint32_t& visits, uint32_t& tests) {
+    const int leaf = r.leaf;
+    if (leaf == WIDE_EMPTY) return;
+    if (++r.steps > 2u * (uint32_t)a.nt + 2u) {
+        atomicOr(a.err, ERR_STACK);
+        r.node = r.leaf = WIDE_EMPTY;
+        return;
+    }
+    if (COUNT) {
+        visits++;
+        tests++;
+    }
+    const float4 p0 = __ldg(&a.tri[3 * leaf]);
+    const float4 p1 = __ldg(&a.tri[3 * leaf + 1]);
+    const float4 p2 = __ldg(&a.tri[3 * leaf + 2]);
+    float t;
+    bool fr;
+    if (ray_tri(r.o, r.d, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                make_float3(p2.x, p2.y, p2.z), t, fr)) {
+        const int idx = __float_as_int(p0.w);
+        if (t < r.bt || (t == r.bt && idx < r.bidx)) {
+            r.bt = t;
+            r.bidx = idx;
+            r.bfront = fr;
         }
     }
-    // pop the next entry that can still hold a hit at distance <= bt
-    while (r.sp > 0) {
-        int nx;
-        float te;
-        stack.pop(--r.sp, nx, te);
-        if (te <= r.bt) {
-            r.node = nx;
-            return false;
-        }
+    r.leaf = WIDE_EMPTY;
+    park_leaves(r, stack);
+}
+
+// One warp iteration of the two-phase traversal for every lane (active or
+// not: call it convergently).  Returns true for a lane whose ray finished.
+template <bool COUNT, class A>
+__device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool active, int leaf_min,
+                                          uint32_t& visits, uint32_t& tests) {
+    if (active) node_step<COUNT>(a, r, stack, visits);
+    const bool parked = active && r.leaf != WIDE_EMPTY;
+    const bool blocked = parked && r.node < 0;             // cannot go on before its leaf
+    const unsigned pm = __ballot_sync(0xFFFFFFFFu, parked);
+    const unsigned bm = __ballot_sync(0xFFFFFFFFu, blocked);
+    const unsigned im = __ballot_sync(0xFFFFFFFFu, active && r.node >= 0);
+    if (pm && (__popc(pm) >= leaf_min || 2 * __popc(bm) >= leaf_min || im == 0)) {
+        if (parked) leaf_step<COUNT>(a, r, stack, visits, tests);
     }
-    return true;
+    return active && ray_done(r);
 }
 
 // Eq. 1 for one texel slot after its rays committed: u_t = min(u, r_t) (the

@@ -37,7 +37,8 @@ rtsdf_status from_cuda_t(cudaError_t e) {
 
 bool valid(const rtsdf_tuning& t) {
     return t.jfa_tile >= 0 && t.jfa_tile <= 3 && t.trace_blocks_per_sm >= 0 && t.refill_min >= 1 &&
-           t.refill_min <= 32 && t.ray_chunk >= 32 && t.ray_chunk <= (1 << 20);
+           t.refill_min <= 32 && t.ray_chunk >= 32 && t.ray_chunk <= (1 << 20) && t.leaf_min >= 1 &&
+           t.leaf_min <= 32;
 }
 
 std::string cache_key(rtsdf_ctx* c) {
@@ -169,6 +170,18 @@ rtsdf_status rtsdf_autotune(rtsdf_t c, float d_vox, int32_t rays, int32_t frame,
         if (e || r == cur.refill_min) continue;
         rtsdf_tuning t = cur;
         t.refill_min = r;
+        float ms = 0.f;
+        e = trial(t, &ms);
+        if (!e && ms < base) {
+            base = ms;
+            cur = t;
+        }
+    }
+    const int leafs[] = {8, 16, 24};
+    for (int lm : leafs) {
+        if (e || lm == cur.leaf_min) continue;
+        rtsdf_tuning t = cur;
+        t.leaf_min = lm;
         float ms = 0.f;
         e = trial(t, &ms);
         if (!e && ms < base) {
