@@ -46,14 +46,17 @@ FLOP_PER_VISIT = 4 * (6 * 2 + 12 + 1) + 5
 FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
-# by the sha256 of the kernel source it was measured on; reported as null
-# once trace.cu changes.
+# by the sha256 of the kernel sources it was measured on; reported as null
+# once trace.cu or trace_dev.cuh changes.
 TRAFFIC = {}
 
 
-def _src_hash(name):
-    p = os.path.join(ROOT, "paper_2210_04449_gb300", "csrc", name)
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+def _src_hash(*names):
+    h = hashlib.sha256()
+    for name in names:
+        p = os.path.join(ROOT, "paper_2210_04449_gb300", "csrc", name)
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -241,7 +244,7 @@ def run_gpu(args, rank, world):
     # node entries include the leaves; a leaf entry is one triangle test
     flop_per_ray = (visits_per_ray - tests_per_ray) * FLOP_PER_VISIT + tests_per_ray * FLOP_PER_TEST
     trace_tflops = rays_frame * flop_per_ray / (trace_ms * 1e-3) / 1e12 if trace_ms else None
-    th = _src_hash("trace.cu")
+    th = _src_hash("trace.cu", "trace_dev.cuh")
     traffic = TRAFFIC.get(th)
 
     line = {
@@ -272,7 +275,13 @@ def run_gpu(args, rank, world):
                 "peak_gbs": hbm_peak, "frac": round(jfa_gbs / hbm_peak, 4) if jfa_gbs else None,
                 "peak_source": hbm_src},
         "tracer": {"node_visits_per_ray": round(visits_per_ray, 2), "tri_tests_per_ray": round(tests_per_ray, 2),
-                   "flop_per_ray": round(flop_per_ray, 1)},
+                   "flop_per_ray": round(flop_per_ray, 1),
+                   # SIMT use of the traversal loop: lanes entering an internal
+                   # node per iteration, lanes testing a triangle per leaf phase
+                   "node_lanes_per_iter": round(32 * (cnt["node_visits"] - cnt["tri_tests"])
+                                                / max(cnt["lane_slots"], 1), 2),
+                   "leaf_lanes_per_phase": round(32 * cnt["tri_tests"] / max(cnt["leaf_slots"], 1), 2),
+                   "leaf_phase_share": round(cnt["leaf_slots"] / max(cnt["lane_slots"], 1), 3)},
         "roofline": {"kernel": "k_trace", "bound": "alu",
                      "achieved": round(trace_tflops, 3) if trace_tflops else None,
                      "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",

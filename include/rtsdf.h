@@ -96,8 +96,12 @@ typedef struct {
     int32_t stage_calls[RTSDF_STAGE_COUNT];
     /* Tracer work since the previous rtsdf_get_stats, only while counting is
        on (rtsdf_set_counting): rays cast, BVH nodes entered, ray/triangle
-       tests. */
+       tests (node_visits includes them); and the SIMT use of the traversal
+       loop: lane slots (32 per warp iteration) of all its iterations and of
+       those that ran the triangle phase.  Internal-node lanes per iteration
+       = (node_visits - tri_tests) / lane_slots x 32. */
     int64_t rays, node_visits, tri_tests;
+    int64_t lane_slots, leaf_slots;
 } rtsdf_stats;
 
 /* Sec. 2: create a context (allocates both grids on the current device).
@@ -257,7 +261,8 @@ rtsdf_status rtsdf_batch_stats(rtsdf_batch_t batch, rtsdf_batch_info* out);
 
 /* Launch parameters of the per-scene path (picked by rtsdf_autotune). */
 typedef struct {
-    int32_t jfa_tile;            /* jump-flood block tile: 0 = 32x8, 1 = 64x4, 2 = 128x2, 3 = 32x4 voxels */
+    int32_t jfa_tile;            /* jump-flood block tile: 0 = 32x8, 1 = 64x4, 2 = 128x2, 3 = 32x4 voxels,
+                                    4 = 32x4 threads flooding 4 voxels each along z (shared z-slices) */
     int32_t trace_blocks_per_sm; /* persistent tracer blocks per SM (0 = occupancy maximum) */
     int32_t refill_min;          /* tracer: refill a warp once this many lanes are idle (1..32) */
     int32_t ray_chunk;           /* tracer: rays a warp takes from the global counter at a time */

@@ -35,7 +35,7 @@ STAGES = ("voxelize", "jfa", "mask", "trace", "bvh", "shadow", "shadow_bwd", "mo
 class Stats(ctypes.Structure):
     _fields_ = [("launches", c_i64), ("n_masked_texels", c_i64), ("jfa_passes", c_i32), ("bvh_depth", c_i32),
                 ("stage_ms", c_f * len(STAGES)), ("stage_calls", c_i32 * len(STAGES)), ("rays", c_i64),
-                ("node_visits", c_i64), ("tri_tests", c_i64)]
+                ("node_visits", c_i64), ("tri_tests", c_i64), ("lane_slots", c_i64), ("leaf_slots", c_i64)]
 
 
 class BatchTuning(ctypes.Structure):

@@ -232,7 +232,8 @@ class RTSDF:
         s = _abi.Stats()
         call("rtsdf_get_stats", self._h, ctypes.byref(s))
         out = {name: getattr(s, name) for name in ("launches", "n_masked_texels", "jfa_passes", "bvh_depth",
-                                                    "rays", "node_visits", "tri_tests")}
+                                                    "rays", "node_visits", "tri_tests", "lane_slots",
+                                                    "leaf_slots")}
         out["stage_ms"] = {k: float(s.stage_ms[i]) for i, k in enumerate(_abi.STAGES)}
         out["stage_calls"] = {k: int(s.stage_calls[i]) for i, k in enumerate(_abi.STAGES)}
         return out

@@ -488,6 +488,8 @@ rtsdf_status rtsdf_get_stats(rtsdf_t c, rtsdf_stats* out) {
     out->rays = (int64_t)tc.rays;
     out->node_visits = (int64_t)tc.visits;
     out->tri_tests = (int64_t)tc.tests;
+    out->lane_slots = (int64_t)tc.slots;
+    out->leaf_slots = (int64_t)tc.leaf_slots;
     return RTSDF_OK;
 }
 

@@ -322,8 +322,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
 
     // ---- stage 5: trace all scenes' rays with dynamic fetch
     unsigned long long* s_rp = s_prefix;
-    __shared__ int s_id[SMEM_STACK][TRACE_THREADS];
-    __shared__ float s_t[SMEM_STACK][TRACE_THREADS];
+    __shared__ int2 s_stack[SMEM_STACK][TRACE_THREADS];
     __syncthreads();   // every thread is done with the voxel prefix
     if (threadIdx.x == 0) {
         unsigned long long acc = 0;
@@ -339,14 +338,14 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
         const unsigned lane = threadIdx.x & 31;
         const unsigned lt = (1u << lane) - 1u;
         int2 deep[TRACE_STACK - SMEM_STACK];
-        Stack stk{&s_id[0][threadIdx.x], &s_t[0][threadIdx.x], deep};
+        Stack stk{&s_stack[0][threadIdx.x], deep};
         Ray r;
         int scene = 0;
         bool active = false;
         unsigned long long chunk_next = 0, chunk_end = 0, chunk_scene_end = 0;
         int chunk_scene = 0;
         bool exhausted = false;
-        uint32_t dummy_v = 0, dummy_t = 0;
+        uint32_t dummy_v = 0, dummy_t = 0, dummy_l = 0;
         for (;;) {
             unsigned idle = __ballot_sync(0xFFFFFFFFu, !active);
             while (idle && !exhausted) {
@@ -390,7 +389,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
             }
             if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
             for (;;) {
-                const bool done = warp_step<false>(b.bvh, r, stk, active, b.leaf_min, dummy_v, dummy_t);
+                const bool done = warp_step<false>(b.bvh, r, stk, active, b.leaf_min, dummy_v, dummy_t, dummy_l);
                 const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
                 if (fin && done) {
                     const unsigned long long key = ((unsigned long long)scene << 32) | r.slot;
@@ -968,7 +967,7 @@ extern "C" rtsdf_status rtsdf_batch_autotune(rtsdf_batch_t b, float d_vox, int32
     };
     float base = 0.f;
     rtsdf_status st = trial(cur, &base);
-    const int refills[] = {2, 4, 8, 16};
+    const int refills[] = {4, 8, 12, 16, 20};
     for (int r : refills) {
         if (st != RTSDF_OK || r == cur.refill_min) continue;
         rtsdf_batch_tuning t = cur;
@@ -980,7 +979,7 @@ extern "C" rtsdf_status rtsdf_batch_autotune(rtsdf_batch_t b, float d_vox, int32
             cur = t;
         }
     }
-    const int leafs[] = {8, 16, 24};
+    const int leafs[] = {8, 12, 16, 24};
     for (int lm : leafs) {
         if (st != RTSDF_OK || lm == cur.leaf_min) continue;
         rtsdf_batch_tuning t = cur;

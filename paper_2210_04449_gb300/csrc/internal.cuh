@@ -41,13 +41,15 @@ struct __align__(16) BNode {
 // 4-wide node collapsed from the binary tree: child boxes SoA (one float4
 // per plane), child ids (>= 0 wide node, < 0 ~leaf), and for the refit the
 // binary source of every child (>= 0 binary node, < 0 ~leaf, WIDE_EMPTY = no
-// child; an empty slot has lo = +inf, hi = -inf and never hits).
+// child; an empty slot has lo = +inf, hi = -inf and never hits).  128 bytes,
+// 32-byte aligned: each (lo, hi) pair of an axis is one 32-byte sector.
 constexpr int WIDE_EMPTY = (int)0x80000000;
-struct __align__(16) WNode {
+struct __align__(32) WNode {
     float4 lox, hix, loy, hiy, loz, hiz;
     int4 child;
     int4 src;
 };
+static_assert(sizeof(WNode) == 128, "4-wide node is 128 bytes");
 
 struct Bvh {
     int64_t nt = 0;
@@ -78,6 +80,7 @@ enum Stage { ST_VOX, ST_JFA, ST_MASK, ST_TRACE, ST_BVH, ST_SHADOW, ST_SHADOW_BWD
 // tracer work counters (device): rays, node visits, triangle tests
 struct TraceCounters {
     unsigned long long rays, visits, tests;
+    unsigned long long slots, leaf_slots;   // lane slots of the traversal iterations / of its leaf phases
 };
 
 }  // namespace rtsdf

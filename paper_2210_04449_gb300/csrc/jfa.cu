@@ -24,8 +24,8 @@ namespace {
 
 // Tiles of 32 x 8 voxels (x, y) per block, one z-plane per grid z.  The 27
 // candidates are read branch-free: an offset that leaves the grid reads the
-// voxel's own coordinate on that axis (always in bounds) and the value is
-// then forced to "no seed".  The arg-min runs in two passes over the 27
+// voxel's own coordinate on that axis (always in bounds), a duplicate of
+// another candidate of the set.  The arg-min runs in two passes over the 27
 // (D2, seed) pairs kept in registers: the smallest D2 first, then the
 // smallest seed among the candidates at that D2 -- the same result as a
 // lexicographic (D2, seed) minimum.
@@ -45,6 +45,80 @@ void launch_pass(rtsdf_ctx* c, const uint32_t* in, uint32_t* out, int n, int k, 
     dim3 block(TX, TY, 1), grid((n + TX - 1) / TX, (n + TY - 1) / TY, n);
     if (final) RTSDF_LAUNCH(c, (k_jfa_pass<true, TX, TY>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
     else RTSDF_LAUNCH(c, (k_jfa_pass<false, TX, TY>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
+}
+
+// z-blocked pass: a thread floods T voxels of one z-lattice column,
+// (x, y, rz + k (T g + t)) for t < T, so the T + 2 candidate z-slices are
+// loaded once and shared (9 (T + 2) loads for 27 T candidates).  Blocks are
+// 32 x 4 threads in (x, y); blockIdx.z = g k + rz.  An x or y offset that
+// leaves the grid reads the voxel's own coordinate on that axis (a duplicate
+// of another candidate), a z-slice outside the grid holds no seed; both
+// leave the arg-min over the voxels inside the grid unchanged.
+template <bool FINAL, int T>
+__global__ void __launch_bounds__(128, 4) k_jfa_zblock(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                      int n, int k, float* __restrict__ coarse, float hc,
+                                                      float beta_h) {
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 4 + threadIdx.y;
+    const int rz = (int)(blockIdx.z % (unsigned)k), g = (int)(blockIdx.z / (unsigned)k);
+    if (x >= n || y >= n) return;
+    const uint32_t n2 = (uint32_t)n * (uint32_t)n;
+    uint32_t xs[3], ys[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int o = (i - 1) * k;
+        xs[i] = (uint32_t)((x + o >= 0 && x + o < n) ? x + o : x);
+        ys[i] = (uint32_t)((y + o >= 0 && y + o < n) ? y + o : y) * (uint32_t)n;
+    }
+    // slice j holds z-lattice index T g + j - 1
+    uint32_t sd[T + 2][9];
+#pragma unroll
+    for (int j = 0; j < T + 2; j++) {
+        const int z = rz + k * (T * g + j - 1);
+        if (z >= 0 && z < n) {
+            const uint32_t zo = (uint32_t)z * n2;
+#pragma unroll
+            for (int iy = 0; iy < 3; iy++)
+#pragma unroll
+                for (int ix = 0; ix < 3; ix++) sd[j][3 * iy + ix] = __ldg(in + zo + ys[iy] + xs[ix]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 9; c++) sd[j][c] = SEED_EMPTY;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        const int z = rz + k * (T * g + t);
+        if (z >= n) break;
+        const uint32_t v = pack_seed(x, y, z);
+        const uint32_t vv = __dp4a(v, v, 0u);
+        uint32_t cd[27];
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int c = 0; c < 9; c++) cd[9 * j + c] = dev::seed_d2(sd[t + j][c], v, vv);
+        uint32_t dmin = __vimin3_u32(cd[0], cd[1], cd[2]);
+#pragma unroll
+        for (int c = 3; c < 27; c += 2) dmin = __vimin3_u32(dmin, cd[c], cd[c + 1]);
+        uint32_t best = SEED_EMPTY;
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int c = 0; c < 9; c++)
+                if (cd[9 * j + c] == dmin) best = min(best, sd[t + j][c]);
+        const uint32_t idx = (uint32_t)x + ys[1] + (uint32_t)z * n2;
+        out[idx] = best;
+        if (FINAL) coarse[idx] = dev::coarse_value(best, dmin, hc, beta_h);
+    }
+}
+
+template <int T>
+void launch_zblock(rtsdf_ctx* c, const uint32_t* in, uint32_t* out, int n, int k, bool final, float beta_h) {
+    const int lat = (n + k - 1) / k;          // z-lattice members of the fullest residue class
+    const int groups = (lat + T - 1) / T;
+    dim3 block(32, 4, 1), grid((n + 31) / 32, (n + 3) / 4, (unsigned)(groups * k));
+    if (final) RTSDF_LAUNCH(c, (k_jfa_zblock<true, T>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
+    else RTSDF_LAUNCH(c, (k_jfa_zblock<false, T>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
 }
 
 // Coarse SDF without a pass (N = 1: no jump steps).
@@ -73,6 +147,10 @@ cudaError_t launch_jfa(rtsdf_ctx* c) {
             case 1: launch_pass<64, 4>(c, in, out, n, k, k == 1, beta_h); break;
             case 2: launch_pass<128, 2>(c, in, out, n, k, k == 1, beta_h); break;
             case 3: launch_pass<32, 4>(c, in, out, n, k, k == 1, beta_h); break;
+            case 4:
+                if ((n + k - 1) / k <= 2) launch_zblock<2>(c, in, out, n, k, k == 1, beta_h);
+                else launch_zblock<4>(c, in, out, n, k, k == 1, beta_h);
+                break;
             default: launch_pass<32, 8>(c, in, out, n, k, k == 1, beta_h); break;
         }
         c->cur ^= 1;

@@ -22,6 +22,10 @@ __device__ __forceinline__ float coarse_value(uint32_t best, uint32_t d2, float 
 }
 
 // One voxel of a pass with step k (27 candidates, two-pass exact arg-min).
+// An offset that leaves the grid is replaced, on that axis only, by offset 0:
+// the voxel read is then another member of the same 27-voxel set, so the
+// arg-min over the multiset equals the arg-min over the voxels inside the
+// grid (voxels outside hold no seed), and no masking is needed.
 // NC: read the input through the read-only path (only when no thread of the
 // launch writes it).
 template <bool FINAL, bool NC>
@@ -30,36 +34,32 @@ __device__ __forceinline__ void jfa_voxel(const uint32_t* __restrict__ in, uint3
     const uint32_t v = pack_seed(x, y, z);
     const uint32_t vv = __dp4a(v, v, 0u);
     int xs[3], ys[3], zs[3];
-    uint32_t mx[3], my[3], mz[3];   // all ones where the offset leaves the grid
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const int o = (i - 1) * k;
-        const bool okx = x + o >= 0 && x + o < n, oky = y + o >= 0 && y + o < n, okz = z + o >= 0 && z + o < n;
-        xs[i] = okx ? x + o : x;
-        ys[i] = oky ? y + o : y;
-        zs[i] = okz ? z + o : z;
-        mx[i] = okx ? 0u : 0xFFFFFFFFu;
-        my[i] = oky ? 0u : 0xFFFFFFFFu;
-        mz[i] = okz ? 0u : 0xFFFFFFFFu;
+        xs[i] = (x + o >= 0 && x + o < n) ? x + o : x;
+        ys[i] = (y + o >= 0 && y + o < n) ? y + o : y;
+        zs[i] = (z + o >= 0 && z + o < n) ? z + o : z;
     }
     uint32_t cs[27], cd[27];
-    uint32_t dmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int iz = 0; iz < 3; iz++) {
 #pragma unroll
         for (int iy = 0; iy < 3; iy++) {
             const uint32_t* row = in + (size_t)n * (ys[iy] + (size_t)n * zs[iz]);
-            const uint32_t mrow = my[iy] | mz[iz];
 #pragma unroll
             for (int ix = 0; ix < 3; ix++) {
                 const int c = 9 * iz + 3 * iy + ix;
-                const uint32_t sv = (NC ? __ldg(row + xs[ix]) : row[xs[ix]]) | mrow | mx[ix];
+                const uint32_t sv = NC ? __ldg(row + xs[ix]) : row[xs[ix]];
                 cs[c] = sv;
                 cd[c] = seed_d2(sv, v, vv);
-                dmin = min(dmin, cd[c]);
             }
         }
     }
+    // smallest D2 (three-input minima), then the smallest seed at that D2
+    uint32_t dmin = __vimin3_u32(cd[0], cd[1], cd[2]);
+#pragma unroll
+    for (int c = 3; c < 27; c += 2) dmin = __vimin3_u32(dmin, cd[c], cd[c + 1]);
     uint32_t best = SEED_EMPTY;
 #pragma unroll
     for (int c = 0; c < 27; c++)

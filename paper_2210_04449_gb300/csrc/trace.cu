@@ -41,16 +41,15 @@ using namespace dev;
 template <bool COUNT>
 __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
     uint32_t n_visits = 0, n_tests = 0, n_rays = 0;
+    uint32_t n_slots = 0, n_leaf_slots = 0;   // COUNT: traversal iterations, leaf phases run
     const uint64_t total = (uint64_t)(*a.count) * 8u * (uint64_t)a.rays;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    // traversal stack: the first SMEM_STACK entries in shared memory laid out
-    // [entry][thread] (each push or pop of a warp touches 32 distinct banks),
-    // deeper entries in local memory
-    __shared__ int s_id[SMEM_STACK][TRACE_THREADS];
-    __shared__ float s_t[SMEM_STACK][TRACE_THREADS];
+    // traversal stack: the first SMEM_STACK (node, distance) entries in shared
+    // memory laid out [entry][thread], deeper entries in local memory
+    __shared__ int2 s_stack[SMEM_STACK][TRACE_THREADS];
     int2 deep[TRACE_STACK - SMEM_STACK];
-    Stack stk{&s_id[0][threadIdx.x], &s_t[0][threadIdx.x], deep};
+    Stack stk{&s_stack[0][threadIdx.x], deep};
     Ray r;
     bool active = false;
     uint64_t chunk_next = 0, chunk_end = 0;   // warp-uniform
@@ -87,7 +86,8 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         // trace until enough lanes are idle to be worth a refill
         for (;;) {
-            const bool done = warp_step<COUNT>(a, r, stk, active, a.leaf_min, n_visits, n_tests);
+            const bool done = warp_step<COUNT>(a, r, stk, active, a.leaf_min, n_visits, n_tests, n_leaf_slots);
+            if (COUNT) n_slots++;
             const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
             if (fin && done) {
                 const unsigned peers = __match_any_sync(fin, r.slot);
@@ -108,16 +108,21 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
         }
     }
     if (COUNT) {
-        unsigned long long rr = n_rays, v = n_visits, t = n_tests;
+        // summed over the warp's lanes, the iteration counts become lane slots
+        unsigned long long rr = n_rays, v = n_visits, t = n_tests, sl = n_slots, ls = n_leaf_slots;
         for (int off = 16; off >= 1; off >>= 1) {
             rr += __shfl_xor_sync(0xFFFFFFFFu, rr, off);
             v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
             t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+            sl += __shfl_xor_sync(0xFFFFFFFFu, sl, off);
+            ls += __shfl_xor_sync(0xFFFFFFFFu, ls, off);
         }
         if (lane == 0) {
             atomicAdd(&a.counters->rays, rr);
             atomicAdd(&a.counters->visits, v);
             atomicAdd(&a.counters->tests, t);
+            atomicAdd(&a.counters->slots, sl);
+            atomicAdd(&a.counters->leaf_slots, ls);
         }
     }
 }

@@ -112,6 +112,27 @@ __device__ __forceinline__ float safe_inv(float d) {
     return __fdividef(1.0f, fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
 }
 
+// 256-bit read-only global load (sm_100 and later) of two float4 at a
+// 32-byte aligned address.
+__device__ __forceinline__ void ldg256(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+// Three-input fp32 maximum / minimum (sm_100 and later); like fmaxf /
+// fminf, a NaN operand is ignored.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Per-lane ray state of the persistent tracer.
 struct Ray {
     float3 o, d, id, oid;
@@ -154,30 +175,24 @@ __device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r
 constexpr int TRACE_THREADS = 128;
 constexpr int SMEM_STACK = 24;
 
+// Traversal stack of one lane: (node, entry distance) pairs, the first
+// SMEM_STACK in shared memory laid out [entry][thread] (a push or pop of a
+// warp is one 64-bit access per lane over distinct banks), deeper entries
+// in local memory.
 struct Stack {
-    int* id;      // &s_id[0][thread], stride TRACE_THREADS
-    float* t;     // &s_t[0][thread]
+    int2* e;      // &s_stack[0][thread], stride TRACE_THREADS
     int2* deep;   // local overflow
     __device__ __forceinline__ void push(int sp, int node, float t0) {
-        if (sp < SMEM_STACK) {
-            id[sp * TRACE_THREADS] = node;
-            t[sp * TRACE_THREADS] = t0;
-        } else {
-            deep[sp - SMEM_STACK] = make_int2(node, __float_as_int(t0));
-        }
+        const int2 v = make_int2(node, __float_as_int(t0));
+        if (sp < SMEM_STACK) e[sp * TRACE_THREADS] = v;
+        else deep[sp - SMEM_STACK] = v;
     }
     __device__ __forceinline__ void pop(int sp, int& node, float& t0) const {
-        if (sp < SMEM_STACK) {
-            node = id[sp * TRACE_THREADS];
-            t0 = t[sp * TRACE_THREADS];
-        } else {
-            const int2 e = deep[sp - SMEM_STACK];
-            node = e.x;
-            t0 = __int_as_float(e.y);
-        }
+        const int2 v = sp < SMEM_STACK ? e[sp * TRACE_THREADS] : deep[sp - SMEM_STACK];
+        node = v.x;
+        t0 = __int_as_float(v.y);
     }
 };
-
 
 // Traversal in two phases.  With one triangle per leaf, a warp in which
 // every lane takes either a node step or a leaf step would pay both paths on
@@ -226,13 +241,20 @@ __device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint
     // Near / far plane rows are chosen by the ray's direction signs (rows:
     // lox, hix, loy, hiy, loz, hiz), so each slab needs no min/max of its two
     // planes; an empty slot (lo = +inf, hi = -inf) never hits.
+    // Each axis's (lo, hi) row pair is one aligned 32-byte sector fetched by
+    // a single 256-bit load: with the lanes of a warp on different nodes, the
+    // L1 data pipe spends one wavefront per lane and sector, not per 16 bytes.
     const WNode* w = a.wide + node;
     const float4* row = &w->lox;
-    const int sx = r.id.x < 0.f, sy = r.id.y < 0.f, sz = r.id.z < 0.f;
-    const float4 nx = __ldg(row + sx), fx = __ldg(row + 1 - sx);
-    const float4 ny = __ldg(row + 2 + sy), fy = __ldg(row + 3 - sy);
-    const float4 nz = __ldg(row + 4 + sz), fz = __ldg(row + 5 - sz);
+    float4 lx, hx, ly, hy, lz, hz;
+    ldg256(row, lx, hx);
+    ldg256(row + 2, ly, hy);
+    ldg256(row + 4, lz, hz);
     const int4 ch = __ldg(&w->child);
+    const bool sx = r.id.x < 0.f, sy = r.id.y < 0.f, sz = r.id.z < 0.f;
+    const float4 nx = sx ? hx : lx, fx = sx ? lx : hx;
+    const float4 ny = sy ? hy : ly, fy = sy ? ly : hy;
+    const float4 nz = sz ? hz : lz, fz = sz ? lz : hz;
     float key[4];
     int val[4] = {ch.x, ch.y, ch.z, ch.w};
     const float bnx[4] = {nx.x, nx.y, nx.z, nx.w}, bfx[4] = {fx.x, fx.y, fx.z, fx.w};
@@ -241,9 +263,9 @@ __device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint
     int nh = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const float t0 = fmaxf(fmaxf(fmaf(bnx[k], r.id.x, -r.oid.x), fmaf(bny[k], r.id.y, -r.oid.y)),
+        const float t0 = fmax3(fmaf(bnx[k], r.id.x, -r.oid.x), fmaf(bny[k], r.id.y, -r.oid.y),
                                fmaxf(fmaf(bnz[k], r.id.z, -r.oid.z), 0.f));
-        const float t1 = fminf(fminf(fmaf(bfx[k], r.id.x, -r.oid.x), fmaf(bfy[k], r.id.y, -r.oid.y)),
+        const float t1 = fmin3(fmaf(bfx[k], r.id.x, -r.oid.x), fmaf(bfy[k], r.id.y, -r.oid.y),
                                fminf(fmaf(bfz[k], r.id.z, -r.oid.z), r.bt));
         const bool hit = t0 <= t1;
         key[k] = hit ? t0 : CUDART_INF_F;
@@ -306,9 +328,11 @@ __device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint
 
 // One warp iteration of the two-phase traversal for every lane (active or
 // not: call it convergently).  Returns true for a lane whose ray finished.
+// COUNT: visits / tests count this lane's node visits and triangle tests,
+// leaf_slots the iterations in which the warp ran its leaf phase.
 template <bool COUNT, class A>
 __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool active, int leaf_min,
-                                          uint32_t& visits, uint32_t& tests) {
+                                          uint32_t& visits, uint32_t& tests, uint32_t& leaf_slots) {
     if (active) node_step<COUNT>(a, r, stack, visits);
     const bool parked = active && r.leaf != WIDE_EMPTY;
     const bool blocked = parked && r.node < 0;             // cannot go on before its leaf
@@ -316,6 +340,7 @@ __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool
     const unsigned bm = __ballot_sync(0xFFFFFFFFu, blocked);
     const unsigned im = __ballot_sync(0xFFFFFFFFu, active && r.node >= 0);
     if (pm && (__popc(pm) >= leaf_min || 2 * __popc(bm) >= leaf_min || im == 0)) {
+        if (COUNT) leaf_slots++;
         if (parked) leaf_step<COUNT>(a, r, stack, visits, tests);
     }
     return active && ray_done(r);

@@ -36,7 +36,7 @@ rtsdf_status from_cuda_t(cudaError_t e) {
 }
 
 bool valid(const rtsdf_tuning& t) {
-    return t.jfa_tile >= 0 && t.jfa_tile <= 3 && t.trace_blocks_per_sm >= 0 && t.refill_min >= 1 &&
+    return t.jfa_tile >= 0 && t.jfa_tile <= 4 && t.trace_blocks_per_sm >= 0 && t.refill_min >= 1 &&
            t.refill_min <= 32 && t.ray_chunk >= 32 && t.ray_chunk <= (1 << 20) && t.leaf_min >= 1 &&
            t.leaf_min <= 32;
 }
@@ -136,7 +136,7 @@ rtsdf_status rtsdf_autotune(rtsdf_t c, float d_vox, int32_t rays, int32_t frame,
     rtsdf_tuning cur = c->tune;
     // jump-flood tile
     float best_ms = 1e30f;
-    for (int tile = 0; tile < 4 && !e; tile++) {
+    for (int tile = 0; tile < 5 && !e; tile++) {
         c->tune = cur;
         c->tune.jfa_tile = tile;
         float ms = 0.f;
@@ -165,7 +165,7 @@ rtsdf_status rtsdf_autotune(rtsdf_t c, float d_vox, int32_t rays, int32_t frame,
     };
     float base = 0.f;
     if (!e) e = trial(cur, &base);
-    const int refills[] = {2, 4, 8, 16};
+    const int refills[] = {4, 8, 12, 16, 20};
     for (int r : refills) {
         if (e || r == cur.refill_min) continue;
         rtsdf_tuning t = cur;
@@ -177,7 +177,7 @@ rtsdf_status rtsdf_autotune(rtsdf_t c, float d_vox, int32_t rays, int32_t frame,
             cur = t;
         }
     }
-    const int leafs[] = {8, 16, 24};
+    const int leafs[] = {8, 12, 16, 24};
     for (int lm : leafs) {
         if (e || lm == cur.leaf_min) continue;
         rtsdf_tuning t = cur;

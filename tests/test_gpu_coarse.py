@@ -29,11 +29,15 @@ def _scenes():
     return {"tiny": tiny, "soup": soup, "room": big, "one": one, "sliver": sliver}
 
 
+@pytest.mark.parametrize("tile", [0, 4])
 @pytest.mark.parametrize("name", ["tiny", "soup", "room", "one", "sliver"])
 @pytest.mark.parametrize("nc", [1, 2, 3, 16, 37, 48])
-def test_voxelize_and_jfa_bit_exact(name, nc):
+def test_voxelize_and_jfa_bit_exact(name, nc, tile):
+    # tile 0: one voxel per thread; tile 4: four voxels per thread sharing
+    # their z-slices (ragged z-lattices at nc = 3, 37, 48)
     m = _scenes()[name]
     rt = _ctx(nc)
+    rt.set_tuning(jfa_tile=tile)
     rt.upload_mesh(m.verts, m.tris)
     rt.voxelize()
     occ_g = seeds_to_linear(rt.grids()["seeds"].cpu().numpy(), nc)
@@ -76,10 +80,13 @@ def test_full_size_room_and_sphere_cloud(nc):
     occ_g = seeds_to_linear(rt.grids()["seeds"].cpu().numpy(), nc)
     occ_o = oracle.voxelize(m.verts, m.tris, BMIN, 1.0, nc)
     assert np.array_equal(occ_g, occ_o)
-    rt.jfa()
-    seeds_g = seeds_to_linear(rt.grids()["seeds"].cpu().numpy(), nc)
     seeds_o, _ = oracle.jfa(occ_o, nc)
-    assert np.array_equal(seeds_g, seeds_o)
+    for tile in range(5):   # every pass kernel the tuner can pick
+        rt.set_tuning(jfa_tile=tile)
+        rt.voxelize()
+        rt.jfa()
+        seeds_g = seeds_to_linear(rt.grids()["seeds"].cpu().numpy(), nc)
+        assert np.array_equal(seeds_g, seeds_o), tile
     rt.sync()
 
 

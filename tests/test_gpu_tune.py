@@ -24,7 +24,7 @@ def _ctx(mesh, nc=48, seed=4):
     return rt
 
 
-@pytest.mark.parametrize("tuning", [dict(jfa_tile=1), dict(jfa_tile=2), dict(jfa_tile=3),
+@pytest.mark.parametrize("tuning", [dict(jfa_tile=1), dict(jfa_tile=2), dict(jfa_tile=3), dict(jfa_tile=4),
                                     dict(refill_min=1, ray_chunk=32), dict(refill_min=16, ray_chunk=4096),
                                     dict(trace_blocks_per_sm=2)])
 def test_tuning_does_not_change_results(tuning):
@@ -52,7 +52,7 @@ def test_autotune_keeps_state_and_results():
     tuned.sync()
     before = _snap(tuned)
     best = tuned.autotune(2.0, 16, 2, use_cache=False)
-    assert 0 <= best["jfa_tile"] <= 3 and best["refill_min"] >= 1 and best["ray_chunk"] >= 32
+    assert 0 <= best["jfa_tile"] <= 4 and best["refill_min"] >= 1 and best["ray_chunk"] >= 32
     after = _snap(tuned)
     for k in ("accum", "counts", "fine"):
         assert np.array_equal(before[k], after[k]), k
