@@ -333,46 +333,55 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
         s_rp[ns] = acc;
     }
     __syncthreads();
+    // per-warp chunk state, kept in shared memory (read only at refills) so
+    // that the traversal loop keeps its registers
+    __shared__ unsigned long long s_cnext[TRACE_THREADS / 32], s_cend[TRACE_THREADS / 32];
+    __shared__ unsigned long long s_csend[TRACE_THREADS / 32];
+    __shared__ int s_cscene[TRACE_THREADS / 32];
     {
-        const unsigned long long total = s_rp[ns];
-        const unsigned lane = threadIdx.x & 31;
+        const unsigned lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
         const unsigned lt = (1u << lane) - 1u;
         int2 deep[TRACE_STACK - SMEM_STACK];
         Stack stk{&s_stack[0][threadIdx.x], deep};
         Ray r;
         int scene = 0;
         bool active = false;
-        unsigned long long chunk_next = 0, chunk_end = 0, chunk_scene_end = 0;
-        int chunk_scene = 0;
         bool exhausted = false;
         uint32_t dummy_v = 0, dummy_t = 0, dummy_l = 0;
+        if (lane == 0) s_cnext[wi] = s_cend[wi] = 0;
+        __syncwarp();
         for (;;) {
             unsigned idle = __ballot_sync(0xFFFFFFFFu, !active);
             while (idle && !exhausted) {
-                if (chunk_next == chunk_end) {
+                unsigned long long cn = s_cnext[wi];
+                if (cn == s_cend[wi]) {
                     unsigned long long c0 = 0;
                     if (lane == 0) c0 = atomicAdd(b.next_ray, (unsigned long long)b.ray_chunk);
                     c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+                    const unsigned long long total = s_rp[ns];
                     if (c0 >= total) {
                         exhausted = true;
                         break;
                     }
-                    chunk_next = c0;
-                    chunk_end = min(c0 + (unsigned long long)b.ray_chunk, total);
-                    // scene of the chunk's first ray and where that scene ends
-                    int cs = 0;
-                    if (lane == 0) cs = find_scene(s_rp, ns, c0);
-                    chunk_scene = __shfl_sync(0xFFFFFFFFu, cs, 0);
-                    chunk_scene_end = s_rp[chunk_scene + 1];
+                    cn = c0;
+                    __syncwarp();
+                    if (lane == 0) {
+                        // scene of the chunk's first ray and where that scene ends
+                        const int cs = find_scene(s_rp, ns, c0);
+                        s_cscene[wi] = cs;
+                        s_csend[wi] = s_rp[cs + 1];
+                        s_cend[wi] = min(c0 + (unsigned long long)b.ray_chunk, total);
+                    }
+                    __syncwarp();
                 }
-                const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
+                const uint32_t avail = (uint32_t)(s_cend[wi] - cn);
                 const uint32_t want = __popc(idle);
                 const uint32_t take = min(avail, want);
                 if (!active) {
                     const uint32_t rank = __popc(idle & lt);
                     if (rank < take) {
-                        const unsigned long long g = chunk_next + rank;
-                        scene = g < chunk_scene_end ? chunk_scene : find_scene(s_rp, ns, g);
+                        const unsigned long long g = cn + rank;
+                        scene = g < s_csend[wi] ? s_cscene[wi] : find_scene(s_rp, ns, g);
                         TraceArgs ta = b.sc[scene].t;
                         ta.rays = P.rays;
                         ta.log2_rays = P.log2_rays;
@@ -384,7 +393,9 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
                         active = true;
                     }
                 }
-                chunk_next += take;
+                __syncwarp();
+                if (lane == 0) s_cnext[wi] = cn + take;
+                __syncwarp();
                 idle = __ballot_sync(0xFFFFFFFFu, !active);
             }
             if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
@@ -415,11 +426,25 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
     stamp(b, 6);
 
     // ---- stage 6: Eq. 1 finalize of every traced texel slot, scene by scene
-    for (int s = 0; s < ns; s++) {
-        const unsigned long long slots = (s_rp[s + 1] - s_rp[s]) >> P.log2_rays;
-        if (tid >= slots) continue;
-        const TraceArgs ta = b.sc[s].t;
-        for (uint64_t g = tid; g < slots; g += nthr) finalize_slot(ta, g);
+    // one grid-stride loop over every scene's slots (slot prefix = ray
+    // prefix >> log2 rays); a thread's slot index only grows, so its scene
+    // index only moves forward
+    {
+        const int lg = P.log2_rays;
+        const unsigned long long stot = s_rp[ns] >> lg;
+        int sc = -1;
+        unsigned long long lo = 0, hi = 0;   // slot range of scene sc
+        TraceArgs ta;
+        for (unsigned long long g = tid; g < stot; g += nthr) {
+            if (g >= hi) {
+                do sc++;
+                while ((s_rp[sc + 1] >> lg) <= g);
+                lo = s_rp[sc] >> lg;
+                hi = s_rp[sc + 1] >> lg;
+                ta = b.sc[sc].t;
+            }
+            finalize_slot(ta, g - lo);
+        }
     }
     grid_barrier(b);
     stamp(b, 7);

@@ -50,15 +50,21 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
     __shared__ int2 s_stack[SMEM_STACK][TRACE_THREADS];
     int2 deep[TRACE_STACK - SMEM_STACK];
     Stack stk{&s_stack[0][threadIdx.x], deep};
+    // per-warp chunk of ray ids, kept in shared memory (read only at refills)
+    // so that the traversal loop keeps its registers
+    __shared__ unsigned long long s_cnext[TRACE_THREADS / 32], s_cend[TRACE_THREADS / 32];
+    const unsigned wi = threadIdx.x >> 5;
+    if (lane == 0) s_cnext[wi] = s_cend[wi] = 0;
+    __syncwarp();
     Ray r;
     bool active = false;
-    uint64_t chunk_next = 0, chunk_end = 0;   // warp-uniform
     bool exhausted = false;                    // warp-uniform
     for (;;) {
         // hand out rays to idle lanes
         unsigned idle = __ballot_sync(0xFFFFFFFFu, !active);
         while (idle && !exhausted) {
-            if (chunk_next == chunk_end) {
+            uint64_t cn = s_cnext[wi];
+            if (cn == s_cend[wi]) {
                 unsigned long long b = 0;
                 if (lane == 0) b = atomicAdd(a.next_ray, (unsigned long long)a.ray_chunk);
                 b = __shfl_sync(0xFFFFFFFFu, b, 0);
@@ -66,21 +72,25 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
                     exhausted = true;
                     break;
                 }
-                chunk_next = b;
-                chunk_end = min((uint64_t)b + (uint64_t)a.ray_chunk, total);
+                cn = b;
+                __syncwarp();
+                if (lane == 0) s_cend[wi] = min((uint64_t)b + (uint64_t)a.ray_chunk, total);
+                __syncwarp();
             }
-            const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
+            const uint32_t avail = (uint32_t)(s_cend[wi] - cn);
             const uint32_t want = __popc(idle);
             const uint32_t take = min(avail, want);
             if (!active) {
                 const uint32_t rank = __popc(idle & lt);
                 if (rank < take) {
-                    setup_ray(a, chunk_next + rank, r);
+                    setup_ray(a, cn + rank, r);
                     active = true;
                     if (COUNT) n_rays++;
                 }
             }
-            chunk_next += take;
+            __syncwarp();
+            if (lane == 0) s_cnext[wi] = cn + take;
+            __syncwarp();
             idle = __ballot_sync(0xFFFFFFFFu, !active);
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;

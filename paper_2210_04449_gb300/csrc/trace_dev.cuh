@@ -354,7 +354,8 @@ __device__ __forceinline__ void finalize_slot(const TraceArgs& a, uint64_t s) {
     const uint32_t parent = a.masked[s >> 3];
     const uint32_t ch = (uint32_t)(s & 7);
     const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
-    const uint32_t px = parent % nc, py = (parent / nc) % nc, pz = parent / (nc * nc);
+    const uint32_t pq = __umulhi(parent, a.nc_mag), pz = __umulhi(pq, a.nc_mag);
+    const uint32_t px = parent - pq * nc, py = pq - pz * nc;
     const uint32_t texel = (2 * px + (ch & 1)) + nf * ((2 * py + ((ch >> 1) & 1)) + nf * (2 * pz + (ch >> 2)));
     const float rmin = __uint_as_float(a.ray_min[s]);
     const uint32_t cv = a.ray_cnt[s];
