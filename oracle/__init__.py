@@ -94,7 +94,8 @@ def _load():
             "orc_point_mesh_distance": (None, [f32p, i32p, c_i64, f64p, c_i64, f64p]),
             "orc_sample": (c_d, [f32p, c_int, f64p, c_d, f64p]),
             "orc_shadow": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
-                                  c_d, c_d, f64p, ctypes.c_void_p]),
+                                  c_d, c_d, f64p, ctypes.c_void_p, ctypes.c_void_p]),
+            "orc_shadow_jitter": (None, [c_u64, c_u32, c_i64, f64p]),
             "orc_shadow_grad": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
                                        c_d, c_d, f64p, f64p, f64p]),
         }
@@ -413,19 +414,50 @@ class FinePipeline:
 # Sec. 2.3 -- soft shadows and their derivative
 # ---------------------------------------------------------------------------
 
-def shadow(sdf, n, bmin, extent, pos, nrm, light_v, k, steps, step_max, eps, info=False):
-    """Visibility per shading point (fp64).  ``sdf`` float32 [n^3]."""
+def shadow(sdf, n, bmin, extent, pos, nrm, light_v, k, steps, step_max, eps, info=False, shift=None):
+    """Visibility per shading point (fp64).  ``sdf`` float32 [n^3].  ``shift``
+    (fp64 [npix], world units, optional) moves each ray origin toward the
+    light: the jitter of Sec. 2.3."""
     s = _f32(sdf).reshape(-1)
     p, q = _f32(pos).reshape(-1, 3), _f32(nrm).reshape(-1, 3)
     npix = p.shape[0]
     vis = np.empty(npix)
     inf = np.empty(3 * npix, np.int32) if info else None
+    sh = None if shift is None else np.ascontiguousarray(shift, np.float64).reshape(-1)
+    if sh is not None and sh.size != npix:
+        raise ValueError("shift needs one value per shading point")
     _load().orc_shadow(s, n, np.asarray(bmin, np.float64), float(extent), p.reshape(-1), q.reshape(-1),
                        npix, np.asarray(light_v, np.float64), float(k), int(steps), float(step_max),
-                       float(eps), vis, inf.ctypes.data if info else None)
+                       float(eps), vis, inf.ctypes.data if info else None,
+                       sh.ctypes.data if sh is not None else None)
     if info:
         return vis, inf.reshape(-1, 3)
     return vis
+
+
+def shadow_jitter(seed, frame, npix):
+    """Per-pixel jitter fractions xi in [0, 1) of one frame (Sec. 2.3: the
+    shadow ray origin is jittered toward the light): Philox-4x32-10 with
+    counter (pixel lo, pixel hi, frame, 0x53484457) and key (seed lo, seed
+    hi), top 24 bits of the first output word times 2^-24."""
+    xi = np.empty(int(npix))
+    _load().orc_shadow_jitter(int(seed) & (2 ** 64 - 1), int(frame) & 0xFFFFFFFF, int(npix), xi)
+    return xi
+
+
+def taa_resolve(cur, hist, blend):
+    """Temporal anti-aliasing of a visibility image (Sec. 2.3 stabilises the
+    jitter noise with TAA), static camera: the history is clamped to the
+    min / max of the current frame's 3x3 neighbourhood (clamped at the image
+    border) and blended toward the current value, out = h + blend (cur - h).
+    ``cur``, ``hist``: [H, W]; fp64 result."""
+    c = np.asarray(cur, np.float64)
+    h = np.asarray(hist, np.float64)
+    H, W = c.shape
+    pad = np.pad(c, 1, mode="edge")
+    win = np.stack([pad[dy:dy + H, dx:dx + W] for dy in range(3) for dx in range(3)])
+    hc = np.clip(h, win.min(axis=0), win.max(axis=0))
+    return hc + float(blend) * (c - hc)
 
 
 def shadow_grad(sdf, n, bmin, extent, pos, nrm, light_v, k, steps, step_max, eps, dvis):

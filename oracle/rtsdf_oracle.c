@@ -715,10 +715,12 @@ static int inside_box(const double* q, const double* bmin, double extent)
  * Returns visibility; *nstep = samples taken, *argmin = step that set res
  * (-1 if none), *term = 1 if stopped by h < eps. */
 static double march_one(const float* f, const march_cfg* mc, const double* p, const double* nrm,
-                        const double* L, double* ts, double* hs, int* nstep, int* argmin, int* term)
+                        const double* L, double shift, double* ts, double* hs, int* nstep, int* argmin,
+                        int* term)
 {
+    /* shift: the origin's jitter toward the light (Sec. 2.3), world units */
     double o[3];
-    for (int a = 0; a < 3; a++) o[a] = p[a] + 2.0 * mc->eps * nrm[a];
+    for (int a = 0; a < 3; a++) o[a] = p[a] + 2.0 * mc->eps * nrm[a] + shift * L[a];
     double t = 0.0, res = 1.0, ph = 1e20;
     int am = -1, i;
     *term = 0;
@@ -756,7 +758,8 @@ static void normalise3(const double* v, double* L)
 EXPORT void orc_shadow(const float* sdf, int n, const double* bmin, double extent,
                        const float* pos, const float* nrm, int64_t npix, const double* light_v,
                        double k, int steps, double step_max, double eps, double* vis,
-                       int32_t* info /* [npix*3] nstep, argmin, term; may be NULL */)
+                       int32_t* info /* [npix*3] nstep, argmin, term; may be NULL */,
+                       const double* shift /* [npix] origin jitter toward L; may be NULL */)
 {
     march_cfg mc = {n, extent / n, extent, eps, k, step_max, steps, bmin};
     double L[3];
@@ -766,8 +769,24 @@ EXPORT void orc_shadow(const float* sdf, int n, const double* bmin, double exten
         double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
         double nn[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
         int ns, am, term;
-        vis[i] = march_one(sdf, &mc, p, nn, L, NULL, NULL, &ns, &am, &term);
+        vis[i] = march_one(sdf, &mc, p, nn, L, shift ? shift[i] : 0.0, NULL, NULL, &ns, &am, &term);
         if (info) { info[3 * i] = ns; info[3 * i + 1] = am; info[3 * i + 2] = term; }
+    }
+}
+
+/* Sec. 2.3 jitters each shadow ray's origin toward the light.  The fraction
+ * xi in [0, 1) of pixel i in frame `frame` is the top 24 bits of the first
+ * word of Philox-4x32-10 (Salmon et al., SC'11) with counter
+ * (i mod 2^32, i div 2^32, frame, 0x53484457 "SHDW") and key (seed lo, seed
+ * hi), times 2^-24 (exact in fp32 and fp64). */
+EXPORT void orc_shadow_jitter(uint64_t seed, uint32_t frame, int64_t npix, double* xi)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < npix; i++) {
+        const uint32_t ctr[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), frame, 0x53484457u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        xi[i] = (double)(w[0] >> 8) * 0x1p-24;
     }
 }
 
@@ -802,7 +821,7 @@ EXPORT void orc_shadow_grad(const float* sdf, int n, const double* bmin, double 
             double p[3] = {pos[3 * pi], pos[3 * pi + 1], pos[3 * pi + 2]};
             double nn[3] = {nrm[3 * pi], nrm[3 * pi + 1], nrm[3 * pi + 2]};
             int ns, am, term;
-            march_one(sdf, &mc, p, nn, L, ts, hs, &ns, &am, &term);
+            march_one(sdf, &mc, p, nn, L, 0.0, ts, hs, &ns, &am, &term);
             if (term || am < 0) continue;
             double o[3];
             for (int a = 0; a < 3; a++) o[a] = p[a] + 2.0 * eps * nn[a];

@@ -10,6 +10,12 @@
 * Umbra and fully-lit special cases.
 * The reverse-mode derivative agrees with fp64 central finite differences
   (step 1e-4) of the forward march, kinks excluded.
+* The jitter of the ray origin toward the light: 24-bit fractions, uniform
+  on [0, 1) and independent across frames; a shifted origin keeps the
+  closed form above and moves the exit step by exactly the shift.
+* The TAA resolve: constant images are fixed points, blend 1 returns the
+  current frame, results stay inside the current 3x3 range, a far history
+  clamps to that range, and an unclamped history decays as (1 - blend)^t.
 """
 import math
 
@@ -143,3 +149,84 @@ def test_gradient_matches_finite_differences():
     for a in range(3):
         fd = float(ws @ central[a])
         assert abs(fd - gl[a]) <= 1e-3 * max(abs(fd), 1e-6), (a, fd, gl[a])
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3's jittered ray origin and the temporal anti-aliasing resolve
+# --------------------------------------------------------------------------
+
+def test_jitter_fractions_uniform_and_per_frame():
+    n = 200_000
+    xi = oracle.shadow_jitter(11, 3, n)
+    assert np.all((xi >= 0) & (xi < 1))
+    assert np.all(xi * 2 ** 24 == np.floor(xi * 2 ** 24))      # 24-bit fractions
+    assert np.array_equal(xi, oracle.shadow_jitter(11, 3, n))  # a function of (seed, frame, pixel)
+    # uniform on [0, 1): Kolmogorov-Smirnov distance against the identity
+    s = np.sort(xi)
+    ks = np.max(np.maximum(np.arange(1, n + 1) / n - s, s - np.arange(n) / n))
+    assert ks < 1.63 / math.sqrt(n)                             # p > 0.01
+    assert abs(xi.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+    other = oracle.shadow_jitter(11, 4, n)                      # another frame
+    assert abs(np.corrcoef(xi, other)[0, 1]) < 5 / math.sqrt(n)
+    assert not np.array_equal(xi, oracle.shadow_jitter(12, 3, n))
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.05, 0.13, 0.31])
+def test_jittered_march_parallel_to_plane_closed_form(shift):
+    # as the closed form above, with the origin moved by `shift` along L:
+    # the march samples o + (shift + t) L, so it leaves the volume after
+    # fewer steps while h and the penumbra terms (in t) stay the same
+    n, H, k, smax_vox, steps = 32, 0.06, 8.0, 4.0, 64
+    h = 1.0 / n
+    y0 = 0.1
+    grid = _linear_grid(n, (0, 1, 0), -y0)
+    eps, smax = h, smax_vox * h
+    p = np.array([[0.1, y0 + H - 2 * eps, 0.5]], np.float32)
+    nrm = np.array([[0, 1, 0]], np.float32)
+    vis = oracle.shadow(grid, n, BMIN, 1.0, p, nrm, (1.0, 0.0, 0.0), k, steps, smax, eps,
+                        shift=np.array([shift]))[0]
+    o = p[0].astype(np.float64) + 2 * eps * nrm[0]
+    Hf = o[1] - y0
+    step = min(Hf, smax)
+    res, last = 1.0, -1
+    for i in range(steps):
+        t = i * step
+        if o[0] + shift + t > 1.0:
+            break
+        last = i
+        if i >= 1 and t - Hf / 2 > 0:
+            res = min(res, k * Hf * math.sqrt(3) / 2 / (t - Hf / 2))
+    assert vis == pytest.approx(res, rel=2e-6, abs=1e-12)
+    # the exit step moves with the shift: ceil((1 - o_x - shift) / step) samples
+    assert last == math.floor((1.0 - o[0] - shift) / step + 1e-12)
+
+
+def test_taa_resolve_rules():
+    rng = np.random.default_rng(5)
+    H, W = 9, 13
+    cur = rng.random((H, W))
+    # a constant image is a fixed point, blend 1 returns the current frame
+    const = np.full((H, W), 0.37)
+    assert np.array_equal(oracle.taa_resolve(const, const, 0.1), const)
+    assert np.allclose(oracle.taa_resolve(cur, rng.random((H, W)), 1.0), cur, atol=0, rtol=0)
+    # the result stays inside the current 3x3 neighbourhood's range
+    hist = rng.uniform(-2, 3, (H, W))
+    out = oracle.taa_resolve(cur, hist, 0.25)
+    for y in range(H):
+        for x in range(W):
+            win = cur[max(y - 1, 0):y + 2, max(x - 1, 0):x + 2]
+            assert win.min() - 1e-15 <= out[y, x] <= win.max() + 1e-15
+    # checkerboard of 0/1 with the history far above: the history clamps to
+    # the neighbourhood maximum 1, so out = 1 + b (cur - 1)
+    cb = (np.add.outer(np.arange(H), np.arange(W)) % 2).astype(np.float64)
+    out = oracle.taa_resolve(cb, np.full((H, W), 10.0), 0.2)
+    assert np.allclose(out, 1.0 + 0.2 * (cb - 1.0), rtol=0, atol=1e-15)
+    # a history inside the range decays geometrically toward a static frame
+    h = np.minimum(cur + 0.01, 1.0)
+    d0 = h - cur
+    for _ in range(6):
+        h = oracle.taa_resolve(cur, h, 0.1)
+    pad = np.pad(cur, 1, mode="edge")
+    mx = np.max([pad[dy:dy + H, dx:dx + W] for dy in range(3) for dx in range(3)], axis=0)
+    inside = (cur + 0.01 <= mx)            # pixels whose first history was not clamped
+    assert np.allclose((h - cur)[inside], (0.9 ** 6 * d0)[inside], rtol=1e-12, atol=1e-15)
