@@ -48,7 +48,11 @@ FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
 # by the sha256 of the kernel sources it was measured on; reported as null
 # once trace.cu or trace_dev.cuh changes.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
+    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch" (1 pass): 7.13 GB + 179.13 MB
+    "4cb47ae20f930ad9": 7.13e9 + 179.13e6,
+}
 
 
 def _src_hash(*names):
@@ -299,17 +303,21 @@ def run_gpu(args, rank, world):
 
 
 def time_shadow(rt, dev, reps=5):
-    """Shadow forward (1920x1080) and adjoint (1024x1024) on the context's
-    fine SDF, CUDA events over `reps` launches each."""
+    """Shadow forward (1920x1080), adjoint (1024x1024), jittered forward +
+    TAA resolve (1920x1080) and the resolve alone, on the context's fine SDF;
+    CUDA events over `reps` launches each."""
     import torch
 
     from synth import scenes as S
     out = {}
     L = (0.4, 1.0, 0.3)
-    for name, (w, h) in (("forward", (1920, 1080)), ("backward", (1024, 1024))):
+    for name, (w, h) in (("forward", (1920, 1080)), ("backward", (1024, 1024)),
+                         ("jittered_taa", (1920, 1080)), ("taa", (1920, 1080))):
         pos, nrm = S.floor_gbuffer(w, h, y=0.02)
         pos_t, nrm_t = torch.tensor(pos, device=dev), torch.tensor(nrm, device=dev)
         vis = torch.empty((h, w), device=dev)
+        hist = torch.zeros((h, w), device=dev)
+        frame = [0]
         if name == "backward":
             dvis = torch.full((h, w), 1.0 / (w * h), device=dev)
             dsdf = torch.zeros(rt.fine_n ** 3, device=dev)
@@ -318,8 +326,15 @@ def time_shadow(rt, dev, reps=5):
         def once():
             if name == "forward":
                 rt.shadow(pos_t, nrm_t, L, k=8.0, steps=64, out=vis)
-            else:
+            elif name == "backward":
                 rt.shadow_backward(pos_t, nrm_t, L, dvis, dsdf, dl, k=8.0, steps=64)
+            elif name == "jittered_taa":
+                # one displayed frame: origin jittered by up to 2 texels, then the resolve
+                rt.shadow(pos_t, nrm_t, L, k=8.0, steps=64, out=vis, jitter_vox=2.0, frame=frame[0])
+                rt.taa_resolve(vis, hist, 1.0 if frame[0] == 0 else 0.1)
+                frame[0] += 1
+            else:
+                rt.taa_resolve(vis, hist, 0.1)
         once()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

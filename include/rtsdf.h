@@ -178,6 +178,30 @@ rtsdf_status rtsdf_shadow(rtsdf_t ctx, const float* sdf, const float* pos, const
                           int64_t npix, const float light[3], float k, int32_t steps,
                           float step_max_vox, float eps_vox, float* vis);
 
+/* Sec. 2.3: rtsdf_shadow with each ray origin jittered toward the light
+ * (the paper jitters the origin to break the pattern of constant step sizes
+ * and steadies the noise with temporal anti-aliasing, see
+ * rtsdf_taa_resolve).  The origin moves by xi x jitter_vox h_f along the
+ * light direction, with xi in [0, 1) from Philox-4x32-10 keyed by the
+ * context seed and counted by (point index, frame); jitter_vox = 0 gives
+ * exactly rtsdf_shadow.  jitter_vox >= 0 and frame >= 0, else RTSDF_E_ARG;
+ * the other arguments as rtsdf_shadow.  Counted in the shadow stage. */
+rtsdf_status rtsdf_shadow_jittered(rtsdf_t ctx, const float* sdf, const float* pos, const float* nrm,
+                                   int64_t npix, const float light[3], float k, int32_t steps,
+                                   float step_max_vox, float eps_vox, float jitter_vox, int32_t frame,
+                                   float* vis);
+
+/* Sec. 2.3: temporal anti-aliasing of a visibility image for a static view.
+ * cur: float32 [height x width] device, this frame (row-major); hist:
+ * float32 [height x width] device, the resolved history, updated in place:
+ * hist = hc + blend (cur - hc), where hc is hist clamped to the min / max of
+ * cur's 3x3 neighbourhood (clamped at the border).  blend in (0, 1]
+ * (1 = take cur, e.g. for the first frame).  cur and hist must not overlap;
+ * a moving view reprojects hist before the call.  RTSDF_E_ARG on bad
+ * sizes, blend or overlapping buffers; an empty image is a no-op. */
+rtsdf_status rtsdf_taa_resolve(rtsdf_t ctx, const float* cur, float* hist, int32_t width, int32_t height,
+                               float blend);
+
 /* Reverse-mode derivative of rtsdf_shadow (the march is recomputed, not
  * stored).  dvis: float32 [npix] dLoss/dvis.  Accumulates (+=) dLoss/dsdf
  * into dsdf (float32 [(2N)^3], caller-zeroed) and dLoss/dlight into

@@ -322,8 +322,8 @@ def eq1_update(u_prev, c_t, r_t, alpha):
 
 def signed_output(u, c_parent, nfront, nback):
     """Fine SDF value of a masked texel: the accumulated minimum (the coarse
-    value while no ray has hit yet), negative when more rays hit back than
-    front faces (Sec. 2.2, last paragraph)."""
+    value while no ray has hit yet), negative when back-face hits outnumber
+    front-face hits (Sec. 2.2, last paragraph)."""
     mag = np.where(np.isfinite(u), u, c_parent)
     return np.where(np.asarray(nback) > np.asarray(nfront), -mag, mag)
 

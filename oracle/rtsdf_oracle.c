@@ -643,8 +643,8 @@ EXPORT void orc_point_mesh_distance(const float* verts, const int32_t* tris, int
  *     if t - y > 0 and k dd / (t - y) < res: res = k dd / (t - y)
  *     ph = h; t += min(h, step_max)
  *   visibility = clamp(res, 0, 1)
- * The penumbra estimate k dd / (t - y) is the "triangulation between the
- * current and previous sample" of Aaltonen (2018) that Sec. 2.3 adopts;
+ * The penumbra estimate k dd / (t - y) combines the current and the
+ * previous sample as in Aaltonen (2018), the estimate Sec. 2.3 adopts;
  * step_max is the restricted maximum step of Sec. 2.3.
  * ====================================================================== */
 

@@ -155,16 +155,32 @@ class RTSDF:
         return (ctypes.c_float * 3)(*l)
 
     def shadow(self, pos, nrm, light, k: float = 8.0, steps: int = 64, step_max_vox: float = 4.0,
-               eps_vox: float = 1.0, sdf=None, out=None):
+               eps_vox: float = 1.0, sdf=None, out=None, jitter_vox: float = 0.0, frame: int = 0):
+        """Soft-shadow visibility per shading point; jitter_vox > 0 jitters
+        each ray origin toward the light (rtsdf_shadow_jittered)."""
         import torch
         pos = pos.contiguous()
         nrm = nrm.contiguous()
         npix = pos.numel() // 3
         vis = out if out is not None else torch.empty(pos.shape[:-1], device=pos.device, dtype=torch.float32)
         sp = 0 if sdf is None else sdf.contiguous().data_ptr()
-        call("rtsdf_shadow", self._h, sp, pos.data_ptr(), nrm.data_ptr(), npix, self._light3(light), float(k),
-             int(steps), float(step_max_vox), float(eps_vox), vis.data_ptr())
+        if jitter_vox:
+            call("rtsdf_shadow_jittered", self._h, sp, pos.data_ptr(), nrm.data_ptr(), npix, self._light3(light),
+                 float(k), int(steps), float(step_max_vox), float(eps_vox), float(jitter_vox), int(frame),
+                 vis.data_ptr())
+        else:
+            call("rtsdf_shadow", self._h, sp, pos.data_ptr(), nrm.data_ptr(), npix, self._light3(light), float(k),
+                 int(steps), float(step_max_vox), float(eps_vox), vis.data_ptr())
         return vis
+
+    def taa_resolve(self, cur, hist, blend: float = 0.1):
+        """In-place temporal anti-aliasing of ``hist`` [H, W] toward ``cur``."""
+        if cur.dim() != 2 or tuple(cur.shape) != tuple(hist.shape) or not hist.is_contiguous():
+            raise ValueError("cur and hist must be [H, W] and hist contiguous")
+        cur = cur.contiguous()
+        call("rtsdf_taa_resolve", self._h, cur.data_ptr(), hist.data_ptr(), int(cur.shape[1]), int(cur.shape[0]),
+             float(blend))
+        return hist
 
     def shadow_backward(self, pos, nrm, light, dvis, dsdf, dlight, k: float = 8.0, steps: int = 64,
                         step_max_vox: float = 4.0, eps_vox: float = 1.0, sdf=None) -> None:

@@ -400,7 +400,35 @@ rtsdf_status rtsdf_shadow(rtsdf_t c, const float* sdf, const float* pos, const f
     if (npix > 0 && !vis) return RTSDF_E_ARG;
     DeviceGuard g(c->device);
     StageTimer tm(c, ST_SHADOW);
-    return from_cuda(launch_shadow(c, sdf, pos, nrm, npix, L, k, steps, smax_vox * c->hf, eps_vox * c->hf, vis));
+    return from_cuda(launch_shadow(c, sdf, pos, nrm, npix, L, k, steps, smax_vox * c->hf, eps_vox * c->hf, 0.f, 0,
+                                   vis));
+}
+
+rtsdf_status rtsdf_shadow_jittered(rtsdf_t c, const float* sdf, const float* pos, const float* nrm, int64_t npix,
+                                   const float light[3], float k, int32_t steps, float smax_vox, float eps_vox,
+                                   float jitter_vox, int32_t frame, float* vis) {
+    float L[3], inv;
+    rtsdf_status s = shadow_common(c, pos, nrm, npix, light, k, steps, smax_vox, eps_vox, L, &inv);
+    if (s != RTSDF_OK) return s;
+    if (npix > 0 && !vis) return RTSDF_E_ARG;
+    if (!(jitter_vox >= 0.f) || !isfinite(jitter_vox) || frame < 0) return RTSDF_E_ARG;
+    DeviceGuard g(c->device);
+    StageTimer tm(c, ST_SHADOW);
+    return from_cuda(launch_shadow(c, sdf, pos, nrm, npix, L, k, steps, smax_vox * c->hf, eps_vox * c->hf,
+                                   jitter_vox * c->hf, frame, vis));
+}
+
+rtsdf_status rtsdf_taa_resolve(rtsdf_t c, const float* cur, float* hist, int32_t width, int32_t height,
+                               float blend) {
+    if (!c || width < 0 || height < 0 || !(blend > 0.f && blend <= 1.f)) return RTSDF_E_ARG;
+    const size_t bytes = (size_t)width * (size_t)height * sizeof(float);
+    if (bytes == 0) return RTSDF_OK;
+    if (!cur || !hist) return RTSDF_E_ARG;
+    const char *a = reinterpret_cast<const char*>(cur), *b = reinterpret_cast<const char*>(hist);
+    if (a < b + bytes && b < a + bytes) return RTSDF_E_ARG;   // in place only on the history
+    DeviceGuard g(c->device);
+    StageTimer tm(c, ST_SHADOW);
+    return from_cuda(launch_taa(c, cur, hist, width, height, blend));
 }
 
 rtsdf_status rtsdf_shadow_backward(rtsdf_t c, const float* sdf, const float* pos, const float* nrm, int64_t npix,

@@ -28,6 +28,7 @@
 #include <math_constants.h>
 
 #include "internal.cuh"
+#include "trace_dev.cuh"   // Philox-4x32-10
 
 namespace rtsdf {
 namespace {
@@ -42,7 +43,18 @@ struct ShadowArgs {
     float Lx, Ly, Lz;
     float k, smax, eps;
     int steps;
+    float jitter;              // origin jitter toward the light, world units (0: none)
+    uint32_t frame, key0, key1;
 };
+
+// Sec. 2.3: the origin moves toward the light by xi x jitter, with xi in
+// [0, 1) the top 24 bits of the first word of Philox-4x32-10, counter
+// (pixel lo, pixel hi, frame, 0x53484457 "SHDW"), key = the context seed.
+__device__ __forceinline__ float jitter_shift(const ShadowArgs& a, long long i) {
+    uint32_t c[4] = {(uint32_t)i, (uint32_t)((unsigned long long)i >> 32), a.frame, 0x53484457u};
+    dev::philox4x32_10(c, a.key0, a.key1);
+    return __fmul_rn(__fmul_rn(__uint2float_rn(c[0] >> 8), 0x1p-24f), a.jitter);
+}
 
 struct Taps {
     int idx[8];
@@ -105,9 +117,15 @@ __global__ void __launch_bounds__(256) k_shadow(ShadowArgs a, float* __restrict_
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= a.npix) return;
     const float two_eps = 2.f * a.eps;
-    const float ox = fmaf(a.nrm[3 * i], two_eps, a.pos[3 * i]);
-    const float oy = fmaf(a.nrm[3 * i + 1], two_eps, a.pos[3 * i + 1]);
-    const float oz = fmaf(a.nrm[3 * i + 2], two_eps, a.pos[3 * i + 2]);
+    float ox = fmaf(a.nrm[3 * i], two_eps, a.pos[3 * i]);
+    float oy = fmaf(a.nrm[3 * i + 1], two_eps, a.pos[3 * i + 1]);
+    float oz = fmaf(a.nrm[3 * i + 2], two_eps, a.pos[3 * i + 2]);
+    if (a.jitter != 0.f) {
+        const float sh = jitter_shift(a, i);
+        ox = fmaf(sh, a.Lx, ox);
+        oy = fmaf(sh, a.Ly, oy);
+        oz = fmaf(sh, a.Lz, oz);
+    }
     float t = 0.f, res = 1.f, ph = 1e20f;
     for (int s = 0; s < a.steps; s++) {
         const float qx = fmaf(t, a.Lx, ox), qy = fmaf(t, a.Ly, oy), qz = fmaf(t, a.Lz, oz);
@@ -225,6 +243,33 @@ __global__ void __launch_bounds__(128) k_shadow_bwd(ShadowArgs a, const float* _
     }
 }
 
+// Temporal anti-aliasing of a visibility image (Sec. 2.3 steadies the
+// jitter noise with TAA), static camera: the history is clamped to the
+// current frame's 3x3 neighbourhood range (clamped at the border) and
+// blended toward the current value in place, h = hc + blend (cur - hc).
+__global__ void __launch_bounds__(256) k_taa(const float* __restrict__ cur, float* __restrict__ hist, int w,
+                                             int h, float blend) {
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= w || y >= h) return;
+    float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+        const int yy = min(max(y + dy, 0), h - 1);
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+            const int xx = min(max(x + dx, 0), w - 1);
+            const float v = __ldg(cur + (size_t)yy * w + xx);
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+    }
+    const size_t i = (size_t)y * w + x;
+    const float c = __ldg(cur + i);
+    const float hc = fminf(fmaxf(hist[i], mn), mx);
+    hist[i] = fmaf(blend, __fsub_rn(c, hc), hc);
+}
+
 ShadowArgs make_args(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm, int64_t npix,
                      const float L[3], float k, int steps, float smax, float eps) {
     ShadowArgs a;
@@ -245,15 +290,22 @@ ShadowArgs make_args(rtsdf_ctx* c, const float* sdf, const float* pos, const flo
     a.smax = smax;
     a.eps = eps;
     a.steps = steps;
+    a.jitter = 0.f;
+    a.frame = 0;
+    a.key0 = (uint32_t)c->cfg.seed;
+    a.key1 = (uint32_t)(c->cfg.seed >> 32);
     return a;
 }
 
 }  // namespace
 
 cudaError_t launch_shadow(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm, int64_t npix,
-                          const float L[3], float k, int steps, float smax, float eps, float* vis) {
+                          const float L[3], float k, int steps, float smax, float eps, float jitter, int frame,
+                          float* vis) {
     if (npix == 0) return cudaSuccess;
     ShadowArgs a = make_args(c, sdf, pos, nrm, npix, L, k, steps, smax, eps);
+    a.jitter = jitter;
+    a.frame = (uint32_t)frame;
     RTSDF_LAUNCH(c, k_shadow, (unsigned)((npix + 255) / 256), 256, 0, a, vis);
     return cudaGetLastError();
 }
@@ -264,6 +316,13 @@ cudaError_t launch_shadow_bwd(rtsdf_ctx* c, const float* sdf, const float* pos, 
     if (npix == 0) return cudaSuccess;
     ShadowArgs a = make_args(c, sdf, pos, nrm, npix, L, k, steps, smax, eps);
     RTSDF_LAUNCH(c, k_shadow_bwd, (unsigned)((npix + 127) / 128), 128, 0, a, dvis, dsdf, dlight, inv_norm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_taa(rtsdf_ctx* c, const float* cur, float* hist, int w, int h, float blend) {
+    if (w == 0 || h == 0) return cudaSuccess;
+    dim3 block(32, 8, 1), grid((unsigned)((w + 31) / 32), (unsigned)((h + 7) / 8), 1);
+    RTSDF_LAUNCH(c, k_taa, grid, block, 0, cur, hist, w, h, blend);
     return cudaGetLastError();
 }
 

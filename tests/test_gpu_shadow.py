@@ -119,3 +119,83 @@ def test_autograd_shadow_fn():
     gs_o, gl_o = oracle.shadow_grad(grid, nf, BMIN, 1.0, pos, nrm, light.detach().numpy(), k=2.0, steps=64,
                                     step_max=4 * h, eps=h, dvis=dvis)
     assert np.max(np.abs(sdf.grad.cpu().numpy() - gs_o)) <= 2e-3 * np.max(np.abs(gs_o)) + 1e-12
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3's jittered ray origin and the TAA resolve
+# --------------------------------------------------------------------------
+
+def _jitter_setup(nf, w, seed):
+    import torch
+    from paper_2210_04449_gb300 import RTSDF
+    rt = RTSDF(nf // 2, seed=seed)
+    grid = _grid(nf)
+    pos, nrm = S.floor_gbuffer(w, w, y=0.1, lo=0.05, hi=0.95)
+    dev = rt.device
+    return rt, grid, pos, nrm, torch.tensor(grid.reshape(-1), device=dev), torch.tensor(pos, device=dev), \
+        torch.tensor(nrm, device=dev)
+
+
+def test_jitter_zero_is_the_plain_march():
+    from paper_2210_04449_gb300.context import call
+    rt, grid, pos, nrm, tg, tp, tn = _jitter_setup(64, 64, 3)
+    L = (0.4, 1.0, 0.3)
+    plain = rt.shadow(tp, tn, L, sdf=tg)
+    jit0 = plain.clone().fill_(-1.0)
+    call("rtsdf_shadow_jittered", rt._h, tg.data_ptr(), tp.data_ptr(), tn.data_ptr(), tp.numel() // 3,
+         rt._light3(L), 8.0, 64, 4.0, 1.0, 0.0, 7, jit0.data_ptr())
+    assert np.array_equal(plain.cpu().numpy(), jit0.cpu().numpy())
+
+
+@pytest.mark.parametrize("nf,jit,frame,seed", [(64, 2.0, 0, 1), (128, 4.0, 5, 2), (64, 0.5, 1 << 20, 3)])
+def test_jittered_shadow_matches_oracle(nf, jit, frame, seed):
+    rt, grid, pos, nrm, tg, tp, tn = _jitter_setup(nf, 96, seed)
+    L = (0.4, 1.0, 0.3)
+    h = 1.0 / nf
+    vis_g = rt.shadow(tp, tn, L, sdf=tg, jitter_vox=jit, frame=frame).cpu().numpy().ravel()
+    shift = oracle.shadow_jitter(seed, frame, pos.reshape(-1, 3).shape[0]) * jit * h
+    vis_o = oracle.shadow(grid, nf, BMIN, 1.0, pos, nrm, L, 8.0, 64, 4 * h, h, shift=shift)
+    plain_o = oracle.shadow(grid, nf, BMIN, 1.0, pos, nrm, L, 8.0, 64, 4 * h, h)
+    d = np.abs(vis_g - vis_o)
+    flips = d > 1e-4
+    print(f"jitter nf={nf} jit={jit}: max|d|={d.max():.2e} flips={flips.sum()}/{d.size} "
+          f"changed-by-jitter={np.mean(np.abs(vis_o - plain_o) > 1e-3):.2f}")
+    assert flips.mean() < 0.01
+    assert np.median(d) < 1e-6
+    assert np.mean(np.abs(vis_o - plain_o) > 1e-3) > 0.01     # the jitter did move the march
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 5), (23, 37), (1080, 1920)])
+@pytest.mark.parametrize("blend", [0.1, 1.0])
+def test_taa_resolve_matches_oracle(H, W, blend):
+    import torch
+    from paper_2210_04449_gb300 import RTSDF
+    rt = RTSDF(8)
+    rng = np.random.default_rng(H * 7 + W)
+    cur = rng.random((H, W)).astype(np.float32)
+    hist = rng.uniform(-0.5, 1.5, (H, W)).astype(np.float32)
+    tc = torch.tensor(cur, device=rt.device)
+    th = torch.tensor(hist, device=rt.device)
+    rt.taa_resolve(tc, th, blend)
+    want = oracle.taa_resolve(cur, hist, blend)
+    assert np.max(np.abs(th.cpu().numpy() - want)) <= 1e-6
+
+
+def test_jittered_shadows_with_taa_over_frames():
+    import torch
+    nf, w, seed, jit = 64, 96, 4, 2.0
+    rt, grid, pos, nrm, tg, tp, tn = _jitter_setup(nf, w, seed)
+    L = (0.4, 1.0, 0.3)
+    h = 1.0 / nf
+    hist_g = torch.zeros((w, w), device=rt.device)
+    hist_o = np.zeros((w, w))
+    for f in range(6):
+        vg = rt.shadow(tp, tn, L, sdf=tg, jitter_vox=jit, frame=f).reshape(w, w)
+        rt.taa_resolve(vg, hist_g, 1.0 if f == 0 else 0.2)
+        shift = oracle.shadow_jitter(seed, f, pos.reshape(-1, 3).shape[0]) * jit * h
+        vo = oracle.shadow(grid, nf, BMIN, 1.0, pos, nrm, L, 8.0, 64, 4 * h, h, shift=shift).reshape(w, w)
+        hist_o = oracle.taa_resolve(vo, hist_o, 1.0 if f == 0 else 0.2)
+    d = np.abs(hist_g.cpu().numpy() - hist_o)
+    print(f"6 jittered frames + TAA: max|d|={d.max():.2e} frac>1e-4={np.mean(d > 1e-4):.4f}")
+    assert np.median(d) < 1e-6
+    assert np.mean(d > 1e-4) < 0.03      # march branch flips, spread by the 3x3 clamp
