@@ -89,7 +89,7 @@ def _load():
                                          ctypes.POINTER(c_f), ctypes.POINTER(c_int)]),
             "orc_texel_centre": (None, [f32p, c_f, c_int, c_i64, f32p]),
             "orc_trace": (None, [f32p, i32p, c_i64, f32p, c_f, c_int, c_u64, c_int, c_int,
-                                 i64p, c_i64, f32p, i32p, i32p, i64p]),
+                                 i64p, c_i64, f32p, i32p, i32p, i64p, i32p]),
             "orc_cast_rays": (None, [f32p, i32p, c_i64, f32p, f32p, c_i64, f32p, i32p, i64p]),
             "orc_point_mesh_distance": (None, [f32p, i32p, c_i64, f64p, c_i64, f64p]),
             "orc_sample": (c_d, [f32p, c_int, f64p, c_d, f64p]),
@@ -263,9 +263,10 @@ def texel_centre(bmin, extent, nf, j):
     return o
 
 
-def trace(verts, tris, bmin, extent, nf, seed, frame, R, texels):
+def trace(verts, tris, bmin, extent, nf, seed, frame, R, texels, nearest=False):
     """One frame of Sec. 2.2 tracing for the given fine texels: (r_t fp32,
-    #front, #back, triangle of r_t)."""
+    #front, #back, triangle of r_t), plus with ``nearest`` the face of the
+    nearest hit (1 = back; on equal distances a front hit wins)."""
     v, t = _f32(verts), _i32(tris)
     tx = np.ascontiguousarray(texels, dtype=np.int64)
     m = tx.size
@@ -273,8 +274,11 @@ def trace(verts, tris, bmin, extent, nf, seed, frame, R, texels):
     nf_ = np.empty(m, np.int32)
     nb = np.empty(m, np.int32)
     bt = np.empty(m, np.int64)
+    rb = np.empty(m, np.int32)
     _load().orc_trace(v.reshape(-1), t.reshape(-1), t.shape[0], _f32(bmin), extent, nf,
-                      int(seed) & (2 ** 64 - 1), frame, R, tx, m, r, nf_, nb, bt)
+                      int(seed) & (2 ** 64 - 1), frame, R, tx, m, r, nf_, nb, bt, rb)
+    if nearest:
+        return r, nf_, nb, bt, rb
     return r, nf_, nb, bt
 
 
@@ -365,16 +369,24 @@ class FinePipeline:
     c and restart their accumulator; masked tracked texels may be reset
     (moved objects), then are traced and updated by Eq. 1."""
 
-    def __init__(self, bmin, extent, nc, beta_vox, d_vox, alpha, seed, track=None):
+    def __init__(self, bmin, extent, nc, beta_vox, d_vox, alpha, seed, track=None, sign="vote"):
+        """sign: "vote" (Sec. 2.2: negative when back-face hits outnumber
+        front-face hits, counts kept over frames) or "nearest" (the variant
+        that keeps the face of the nearest hit found so far; on equal
+        distances a front hit wins)."""
+        if sign not in ("vote", "nearest"):
+            raise ValueError(sign)
         self.bmin = np.asarray(bmin, np.float32)
         self.extent = float(extent)
         self.nc, self.nf = nc, 2 * nc
         self.beta, self.d, self.alpha, self.seed = beta_vox, d_vox, alpha, seed
+        self.sign = sign
         self.track = None if track is None else np.asarray(track, np.int64)
         m = self.nf ** 3 if track is None else self.track.size
         self.u = np.full(m, np.inf)
         self.nF = np.zeros(m, np.int64)
         self.nB = np.zeros(m, np.int64)
+        self.back = np.zeros(m, np.int64)   # "nearest": face of the accumulated minimum
         self.f = np.zeros(m)
 
     def texels(self):
@@ -392,6 +404,7 @@ class FinePipeline:
         self.u[~m] = np.inf
         self.nF[~m] = 0
         self.nB[~m] = 0
+        self.back[~m] = 0
         self.f[~m] = fun[tx][~m]
         sel = np.nonzero(m)[0]
         if moved_aabbs is not None and sel.size:
@@ -401,12 +414,27 @@ class FinePipeline:
             self.u[sel[rs]] = np.inf
             self.nF[sel[rs]] = 0
             self.nB[sel[rs]] = 0
+            self.back[sel[rs]] = 0
         if sel.size:
-            r, cf, cb, _ = trace(verts, tris, self.bmin, self.extent, self.nf, self.seed, frame, R, tx[sel])
-            self.u[sel] = eq1_update(self.u[sel], cpar[sel], r, self.alpha)
-            self.nF[sel] += cf
-            self.nB[sel] += cb
-            self.f[sel] = signed_output(self.u[sel], cpar[sel], self.nF[sel], self.nB[sel])
+            r, cf, cb, _, rb = trace(verts, tris, self.bmin, self.extent, self.nf, self.seed, frame, R, tx[sel],
+                                     nearest=True)
+            if self.sign == "vote":
+                self.u[sel] = eq1_update(self.u[sel], cpar[sel], r, self.alpha)
+                self.nF[sel] += cf
+                self.nB[sel] += cb
+                self.f[sel] = signed_output(self.u[sel], cpar[sel], self.nF[sel], self.nB[sel])
+            else:
+                # Eq. 1's minimum, keeping the face of whichever term is smaller
+                # (the decayed previous value or this frame's nearest hit)
+                prev = eq1_update(self.u[sel], cpar[sel], np.full(sel.size, np.inf), self.alpha)
+                r64 = r.astype(np.float64)
+                bp = self.back[sel]
+                back = np.where(r64 < prev, rb, np.where(prev < r64, bp, np.minimum(bp, rb)))
+                u = np.minimum(prev, r64)
+                self.u[sel] = u
+                self.back[sel] = np.where(np.isfinite(u), back, 0)
+                mag = np.where(np.isfinite(u), u, cpar[sel])
+                self.f[sel] = np.where(self.back[sel] == 1, -mag, mag)
         return dict(occ=occ, seeds=seeds, c=c, mask=mask)
 
 

@@ -513,7 +513,8 @@ EXPORT void orc_texel_centre(const float* bmin, float extent, int nf, int64_t j,
 EXPORT void orc_trace(const float* verts, const int32_t* tris, int64_t nt, const float* bmin,
                       float extent, int nf, uint64_t seed, int frame, int R,
                       const int64_t* texels, int64_t m, float* rmin, int32_t* nfront,
-                      int32_t* nback, int64_t* best_tri)
+                      int32_t* nback, int64_t* best_tri,
+                      int32_t* min_back /* face of the nearest hit (1 = back), ties -> front; may be NULL */)
 {
     float* tv0 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
     float* te1 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
@@ -524,7 +525,7 @@ EXPORT void orc_trace(const float* verts, const int32_t* tris, int64_t nt, const
         float o[3];
         orc_texel_centre(bmin, extent, nf, texels[i], o);
         float r = INFINITY;
-        int32_t cf = 0, cb = 0;
+        int32_t cf = 0, cb = 0, rb = 0;
         int64_t bt = -1;
         for (int ray = 0; ray < R; ray++) {
             float d[3], t;
@@ -533,12 +534,14 @@ EXPORT void orc_trace(const float* verts, const int32_t* tris, int64_t nt, const
             int64_t hit = closest_hit(o, d, tv0, te1, te2, nt, &t, &f);
             if (hit < 0) continue;
             if (f) cf++; else cb++;
-            if (t < r) { r = t; bt = hit; }
+            if (t < r) { r = t; bt = hit; rb = !f; }
+            else if (t == r && f) rb = 0;   /* equal nearest distance: a front hit wins */
         }
         rmin[i] = r;
         nfront[i] = cf;
         nback[i] = cb;
         if (best_tri) best_tri[i] = bt;
+        if (min_back) min_back[i] = rb;
     }
     free(tv0); free(te1); free(te2);
 }

@@ -216,3 +216,61 @@ def test_eq1_and_sign_and_reset_rules():
     hi = np.array([[0.7, 0.6, 0.6]], np.float32)
     assert list(oracle.reset_rule(p, np.array([0.11, 0.1]), lo, hi)) == [True, False]
     assert list(oracle.reset_rule(p, np.array([0.09, 0.21]), lo, hi)) == [False, True]
+
+
+# --------------------------------------------------------------------------
+# The nearest-hit sign variant (the face of the nearest hit found so far)
+# --------------------------------------------------------------------------
+
+def _box_pipeline(mesh, nc, sign, R=16, frames=2):
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, 0.5, 2.0, 1.0, 9, sign=sign)
+    for f in range(frames):
+        pipe.frame(mesh.verts, mesh.tris, f, R)
+    return pipe
+
+
+def test_nearest_sign_inside_and_outside_a_closed_box():
+    # every first hit from inside a closed, outward-facing box is a back face
+    # and every first hit from outside one is a front face
+    m = S.merge([S.box_mesh((0.5, 0.5, 0.5), 0.25)])
+    nc = 16
+    vote = _box_pipeline(m, nc, "vote")
+    near = _box_pipeline(m, nc, "nearest")
+    tx = near.texels()
+    hit = np.isfinite(near.u)
+    assert hit.sum() > 1000
+    assert np.array_equal(near.u, vote.u)               # same rays, same minimum
+    nf = 2 * nc
+    cen = (np.stack([tx % nf, (tx // nf) % nf, tx // (nf * nf)], 1) + 0.5) / nf
+    inside = np.all(np.abs(cen - 0.5) < 0.25, axis=1)
+    assert np.all(near.f[hit & inside] < 0) and np.all(near.f[hit & ~inside] > 0)
+
+
+def test_nearest_sign_follows_the_closest_ray_not_the_vote():
+    # texels inside a big closed box, just behind a small front-facing plate:
+    # most rays end on the box walls (back faces), so the vote is negative,
+    # while the nearest hit is the plate's front face whenever some ray meets it
+    plate = (np.array([[0.40, 0.5, 0.40], [0.62, 0.5, 0.45], [0.45, 0.5, 0.62]], np.float64),
+             np.array([[0, 1, 2]], np.int64))                    # normal -y (faces the texels below)
+    m = S.merge([S.box_mesh((0.5, 0.5, 0.5), 0.45), plate])
+    nc, R = 16, 4            # few rays: some texels meet the plate in one frame only
+    nf = 2 * nc
+    vote = _box_pipeline(m, nc, "vote", R=R, frames=2)
+    near = _box_pipeline(m, nc, "nearest", R=R, frames=2)
+    tx = near.texels()
+    cen = (np.stack([tx % nf, (tx // nf) % nf, tx // (nf * nf)], 1) + 0.5) / nf
+    below = (np.abs(cen[:, 1] - 0.47) < 0.02) & (np.abs(cen[:, 0] - 0.48) < 0.03) & \
+            (np.abs(cen[:, 2] - 0.48) < 0.03) & np.isfinite(near.u)
+    assert below.sum() >= 4
+    # independent check: cast the texel's rays of both frames one by one and
+    # take the face of the closest one (ties: front)
+    for i in np.nonzero(below)[0]:
+        o = cen[i].astype(np.float32)
+        dirs = np.stack([oracle.sphere_dir(9, int(tx[i]), f, r)[0] for f in range(2) for r in range(R)])
+        t, front, _ = oracle.cast_rays(m.verts, m.tris, np.repeat(o[None], 2 * R, 0), dirs)
+        tmin = t.min()
+        want_back = 0 if np.any(front[t == tmin]) else 1
+        assert near.u[i] == tmin
+        assert (near.f[i] < 0) == bool(want_back)
+    assert np.any(near.f[below] > 0) and np.any(vote.f[below] < 0)
+    assert np.any((near.f[below] > 0) & (vote.f[below] < 0))   # the two statistics differ here
