@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--impl", default="rtsdf", choices=["rtsdf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form comparison")
+    ap.add_argument("--no-variant", action="store_true", help="skip the nearest-face sign variant comparison")
     ap.add_argument("--objects", type=int, default=N_OBJ, help="sphere count (500 = the 1M-triangle workload)")
     ap.add_argument("--coarse-n", type=int, default=NC, help="coarse grid size (256 = the benchmark workload; "
                                                               "smaller only for profiling captures)")
@@ -349,6 +350,56 @@ def time_shadow(rt, dev, reps=5):
     return out
 
 
+def run_sign_variant(dev, frames=8, rays=RAYS, nc=128):
+    """The nearest-face sign variant (rays capped at the texel's running
+    minimum) against Sec. 2.2's vote on the static room scene (128^3 ->
+    256^3, ~100k triangles): trace ms of the first frame and of the later
+    frames, work per ray from a counted last frame, and how the two compare
+    (the distances must be identical, the signs may differ)."""
+    import numpy as np
+
+    from paper_2210_04449_gb300 import RTSDF
+    from synth import scenes as S
+    mesh = S.room_scene(1)
+    out, grids = {}, {}
+    for mode in ("vote", "nearest"):
+        rt = RTSDF(nc, beta_vox=BETA, seed=SEED)
+        rt.set_sign_mode(mode)
+        rt.upload_mesh(mesh.verts, mesh.tris)
+        rt.build_bvh()
+        rt.set_profiling(True)
+        per = []
+        for f in range(frames):
+            last = f == frames - 1
+            rt.set_counting(last)
+            rt.stats()
+            rt.update(D_VOX, rays, f)
+            rt.sync()
+            st = rt.stats()
+            if not last:
+                per.append(st["stage_ms"]["trace"])
+            else:
+                cnt = st
+        rt.set_counting(False)
+        g = rt.grids()
+        grids[mode] = (g["accum"].cpu().numpy(), g["fine"].cpu().numpy())
+        out[mode] = {"first_frame_trace_ms": round(per[0], 3),
+                     "later_frames_trace_ms": round(float(np.mean(per[2:])), 3),
+                     "node_visits_per_ray": round(cnt["node_visits"] / max(cnt["rays"], 1), 2),
+                     "tri_tests_per_ray": round(cnt["tri_tests"] / max(cnt["rays"], 1), 2)}
+        rt.close()
+    uv, fv = grids["vote"]
+    un, fn = grids["nearest"]
+    hit = np.isfinite(uv)
+    out["workload"] = (f"static room {nc}^3->{2 * nc}^3, {mesh.nt:,} tris, {rays} rays/texel, {frames} frames "
+                       f"(later = frames 2..{frames - 2}; the last frame is counted, untimed)")
+    out["distances_identical"] = bool(np.array_equal(uv, un))
+    out["sign_agreement"] = round(float(np.mean(np.sign(fv[hit]) == np.sign(fn[hit]))), 5) if hit.any() else None
+    out["later_frames_speedup"] = round(out["vote"]["later_frames_trace_ms"]
+                                        / max(out["nearest"]["later_frames_trace_ms"], 1e-9), 2)
+    return out
+
+
 def run_batched(dev, frames=3, rays=32, d_vox=2.0):
     """The batched form against plain per-scene frames on 64 uneven scenes
     (coarse 32..128, 1k-200k triangles): ms/frame for all scenes, and whether
@@ -500,6 +551,9 @@ def main():
     if not args.no_batch:
         import torch
         line["batched"] = run_batched(torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+    if not args.no_variant:
+        import torch
+        line["sign_variant"] = run_sign_variant(torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             ms, info = oracle_frame_sample(16, masked_texels=m_tex)

@@ -165,6 +165,23 @@ rtsdf_status rtsdf_jfa(rtsdf_t ctx);
  * restart their accumulation.  Requires rtsdf_jfa and rtsdf_build_bvh. */
 rtsdf_status rtsdf_trace(rtsdf_t ctx, float d_vox, int32_t rays_per_texel, int32_t frame);
 
+/* Sign statistic of the fine SDF.
+ * RTSDF_SIGN_VOTE (default, Sec. 2.2): a texel is negative when its rays'
+ *   back-face hits outnumber its front-face hits, counted over frames.
+ * RTSDF_SIGN_NEAREST (a variant, not in the paper): a texel takes the face of
+ *   the nearest hit found so far (on equal distances a front hit wins), so
+ *   no ray needs to look beyond the texel's accumulated distance u: each ray
+ *   starts with u as its best hit and culls everything farther.  The
+ *   distances u are those of the vote mode (the same rays, the same minimum);
+ *   only the sign statistic differs.  In this mode the counts grid holds the
+ *   face bit (1 = back) instead of the hit counts.
+ * Changing the mode restarts the accumulation (u = +inf, counts 0, f 0);
+ * saved states record their mode and rtsdf_load_state adopts it.
+ * RTSDF_E_ARG for an unknown mode. */
+typedef enum { RTSDF_SIGN_VOTE = 0, RTSDF_SIGN_NEAREST = 1 } rtsdf_sign_mode;
+rtsdf_status rtsdf_set_sign_mode(rtsdf_t ctx, int32_t mode);
+rtsdf_status rtsdf_get_sign_mode(rtsdf_t ctx, int32_t* mode);
+
 /* Sec. 2.3: soft-shadow visibility.  sdf: float32 [(2N)^3] device grid
  * (NULL = the context's fine SDF).  pos, nrm: float32 [npix, 3] device
  * shading points and unit normals.  light: direction towards the light

@@ -240,6 +240,19 @@ class RTSDF:
              ctypes.byref(t))
         return {k: getattr(t, k) for k, _ in _abi.Tuning._fields_}
 
+    SIGN_MODES = {"vote": 0, "nearest": 1}
+
+    def set_sign_mode(self, mode: str) -> None:
+        """"vote" (Sec. 2.2's front/back vote) or "nearest" (the face of the
+        nearest hit; rays capped at the texel's accumulated distance).
+        Changing the mode restarts the accumulation."""
+        call("rtsdf_set_sign_mode", self._h, self.SIGN_MODES[mode])
+
+    def get_sign_mode(self) -> str:
+        v = ctypes.c_int32()
+        call("rtsdf_get_sign_mode", self._h, ctypes.byref(v))
+        return {0: "vote", 1: "nearest"}[v.value]
+
     def set_counting(self, on: bool) -> None:
         call("rtsdf_set_counting", self._h, int(bool(on)))
 

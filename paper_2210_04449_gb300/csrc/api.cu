@@ -96,6 +96,16 @@ cudaError_t reset_temporal(rtsdf_ctx* c) {
     return e;
 }
 
+// Per-slot frame scratch back to "nothing committed" for the context's sign
+// mode (after a mode change).
+cudaError_t reset_scratch(rtsdf_ctx* c) {
+    const bool nearest = c->sign_mode == RTSDF_SIGN_NEAREST;
+    cudaError_t e = nearest ? cudaMemsetAsync(c->ray_min, 0xFF, 8 * c->nc3 * sizeof(uint32_t), c->stream)
+                            : fill_f32(c, reinterpret_cast<float*>(c->ray_min), 8 * c->nc3, INFINITY);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ray_cnt, 0, 8 * c->nc3 * sizeof(uint32_t), c->stream);
+    return e;
+}
+
 // sum the recorded event pairs of one stage into its carry (waits for them)
 void drain(Timer& t) {
     for (int i = 0; i < t.n; i++) {
@@ -536,7 +546,7 @@ rtsdf_status rtsdf_save_state(rtsdf_t c, void* host_buf, size_t bytes) {
     if (bytes < need) return RTSDF_E_ARG;
     DeviceGuard g(c->device);
     uint8_t* p = (uint8_t*)host_buf;
-    uint32_t hdr[4] = {STATE_MAGIC, 1u, (uint32_t)c->nc, 0u};
+    uint32_t hdr[4] = {STATE_MAGIC, 1u, (uint32_t)c->nc, (uint32_t)c->sign_mode};
     memcpy(p, hdr, 16);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (!e) e = cudaMemcpy(p + 16, c->accum, c->nf3 * sizeof(float), cudaMemcpyDeviceToHost);
@@ -554,12 +564,34 @@ rtsdf_status rtsdf_load_state(rtsdf_t c, const void* host_buf, size_t bytes) {
     uint32_t hdr[4];
     memcpy(hdr, p, 16);
     if (hdr[0] != STATE_MAGIC || hdr[1] != 1u || hdr[2] != (uint32_t)c->nc) return RTSDF_E_ARG;
+    if (hdr[3] != RTSDF_SIGN_VOTE && hdr[3] != RTSDF_SIGN_NEAREST) return RTSDF_E_ARG;
     DeviceGuard g(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (!e && (int)hdr[3] != c->sign_mode) {
+        c->sign_mode = (int)hdr[3];   // the state carries its sign mode
+        e = reset_scratch(c);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+    }
     if (!e) e = cudaMemcpy(c->accum, p + 16, c->nf3 * sizeof(float), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->counts, p + 16 + c->nf3 * 4, c->nf3 * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->fine, p + 16 + c->nf3 * 8, c->nf3 * sizeof(float), cudaMemcpyHostToDevice);
     return from_cuda(e);
+}
+
+rtsdf_status rtsdf_set_sign_mode(rtsdf_t c, int32_t mode) {
+    if (!c || (mode != RTSDF_SIGN_VOTE && mode != RTSDF_SIGN_NEAREST)) return RTSDF_E_ARG;
+    if (mode == c->sign_mode) return RTSDF_OK;
+    DeviceGuard g(c->device);
+    c->sign_mode = mode;
+    cudaError_t e = reset_temporal(c);   // the counts word changes meaning: restart accumulation
+    if (!e) e = reset_scratch(c);
+    return from_cuda(e);
+}
+
+rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
+    if (!c || !mode) return RTSDF_E_ARG;
+    *mode = c->sign_mode;
+    return RTSDF_OK;
 }
 
 rtsdf_status rtsdf_sync(rtsdf_t c) {

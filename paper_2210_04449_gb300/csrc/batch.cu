@@ -405,15 +405,8 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
                 if (fin && done) {
                     const unsigned long long key = ((unsigned long long)scene << 32) | r.slot;
                     const unsigned peers = __match_any_sync(fin, key);
-                    const bool hit = r.bidx != 0x7FFFFFFF;
-                    const uint32_t tb = hit ? (__float_as_uint(r.bt) & 0x7FFFFFFFu) : 0x7F800000u;
-                    const uint32_t cv = hit ? (r.bfront ? 1u : 0x10000u) : 0u;
-                    const uint32_t mn = __reduce_min_sync(peers, tb);
-                    const uint32_t sum = __reduce_add_sync(peers, cv);
-                    if ((peers & lt) == 0) {
-                        if (mn != 0x7F800000u) atomicMin(b.sc[scene].t.ray_min + r.slot, mn);
-                        if (sum) atomicAdd(b.sc[scene].t.ray_cnt + r.slot, sum);
-                    }
+                    const TraceArgs& st = b.sc[scene].t;
+                    commit_ray(r, st.nearest != 0, peers, lt, st.ray_min, st.ray_cnt);
                     active = false;
                 }
                 const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
@@ -571,6 +564,7 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
         d.passes = L;
         d.nmag = (uint32_t)((0x100000000ull + (unsigned long long)c->nc - 1) / (unsigned long long)c->nc);
         d.t.nc_mag = d.nmag;
+        d.t.nearest = c->sign_mode == RTSDF_SIGN_NEAREST;
         maxp = L > maxp ? L : maxp;
         vp[s] = av;
         tp[s] = at;

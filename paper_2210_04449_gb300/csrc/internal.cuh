@@ -144,6 +144,7 @@ struct rtsdf_ctx {
     unsigned trace_grid = 0;
 
     // launch parameters (rtsdf_set_tuning / rtsdf_autotune)
+    int sign_mode = RTSDF_SIGN_VOTE;   // rtsdf_set_sign_mode
     rtsdf_tuning tune = {0, 0, 16, 1024, 16};
 
     rtsdf::Bvh bvh;

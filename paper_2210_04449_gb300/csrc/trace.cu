@@ -101,15 +101,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
             const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
             if (fin && done) {
                 const unsigned peers = __match_any_sync(fin, r.slot);
-                const bool hit = r.bidx != 0x7FFFFFFF;
-                const uint32_t tb = hit ? (__float_as_uint(r.bt) & 0x7FFFFFFFu) : 0x7F800000u;
-                const uint32_t cv = hit ? (r.bfront ? 1u : 0x10000u) : 0u;
-                const uint32_t mn = __reduce_min_sync(peers, tb);
-                const uint32_t sum = __reduce_add_sync(peers, cv);
-                if ((peers & lt) == 0) {
-                    if (mn != 0x7F800000u) atomicMin(a.ray_min + r.slot, mn);
-                    if (sum) atomicAdd(a.ray_cnt + r.slot, sum);
-                }
+                commit_ray(r, a.nearest != 0, peers, lt, a.ray_min, a.ray_cnt);
                 active = false;
             }
             const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
@@ -182,6 +174,7 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.ray_chunk = c->tune.ray_chunk;
     a.leaf_min = c->tune.leaf_min;
     a.nc_mag = (uint32_t)((0x100000000ull + (unsigned long long)c->nc - 1) / (unsigned long long)c->nc);
+    a.nearest = c->sign_mode == RTSDF_SIGN_NEAREST;
     cudaError_t e = cudaMemsetAsync(c->d_next_ray, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     {

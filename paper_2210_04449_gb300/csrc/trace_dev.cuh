@@ -33,7 +33,12 @@ struct TraceArgs {
     int ray_chunk;             // rays a warp takes from the global counter at a time
     int leaf_min;              // run the leaf phase once this many lanes hold a parked leaf
     uint32_t nc_mag;           // ceil(2^32 / nc): umulhi(v, nc_mag) = v / nc for v < 2^24
+    int nearest;               // sign from the nearest hit's face; rays capped at the texel's u
 };
+
+// Per-slot "nothing committed" value of ray_min: +inf bits for the vote,
+// all ones for the nearest-face key (t bits << 1 | back).
+__host__ __device__ constexpr uint32_t ray_min_none(bool nearest) { return nearest ? 0xFFFFFFFFu : 0x7F800000u; }
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -156,13 +161,17 @@ __device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r
     const uint32_t px = parent - pq * nc, py = pq - pz * nc;
     const uint32_t jx = 2 * px + (ch & 1), jy = 2 * py + ((ch >> 1) & 1), jz = 2 * pz + (ch >> 2);
     const uint32_t texel = jx + nf * (jy + nf * jz);
+    // nearest-face variant: no hit beyond the texel's accumulated distance
+    // can change its result, so the ray starts with that distance as its
+    // best hit (hits at exactly that distance still count: bidx is unset)
+    const float cap = a.nearest ? a.accum[texel] : CUDART_INF_F;
     r.o = make_float3(__fadd_rn(a.bx, __fmul_rn(__fadd_rn((float)jx, 0.5f), a.hf)),
                       __fadd_rn(a.by, __fmul_rn(__fadd_rn((float)jy, 0.5f), a.hf)),
                       __fadd_rn(a.bz, __fmul_rn(__fadd_rn((float)jz, 0.5f), a.hf)));
     r.d = sphere_dir(a.key0, a.key1, texel, a.frame, ray);
     r.id = make_float3(safe_inv(r.d.x), safe_inv(r.d.y), safe_inv(r.d.z));
     r.oid = make_float3(r.o.x * r.id.x, r.o.y * r.id.y, r.o.z * r.id.z);
-    r.bt = CUDART_INF_F;
+    r.bt = cap;
     r.bidx = 0x7FFFFFFF;
     r.bfront = false;
     r.node = a.nt > 1 ? 0 : (a.nt == 1 ? ~0 : WIDE_EMPTY);   // no triangles: nothing to enter
@@ -346,6 +355,30 @@ __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool
     return active && ray_done(r);
 }
 
+// Commit of finished rays that share a texel slot (peers: the lanes of the
+// same slot among those finishing now; lt: lanes below this one).  Vote:
+// the minimum distance bits and the front | back << 16 hit counts.
+// Nearest face: the minimum of (distance bits << 1 | back), ties -> front.
+__device__ __forceinline__ void commit_ray(const Ray& r, bool nearest, unsigned peers, unsigned lt,
+                                           uint32_t* ray_min, uint32_t* ray_cnt) {
+    const bool hit = r.bidx != 0x7FFFFFFF;
+    const uint32_t tbits = __float_as_uint(r.bt) & 0x7FFFFFFFu;
+    if (nearest) {
+        const uint32_t key = hit ? ((tbits << 1) | (r.bfront ? 0u : 1u)) : 0xFFFFFFFFu;
+        const uint32_t mn = __reduce_min_sync(peers, key);
+        if ((peers & lt) == 0 && mn != 0xFFFFFFFFu) atomicMin(ray_min + r.slot, mn);
+        return;
+    }
+    const uint32_t tb = hit ? tbits : 0x7F800000u;
+    const uint32_t cv = hit ? (r.bfront ? 1u : 0x10000u) : 0u;
+    const uint32_t mn = __reduce_min_sync(peers, tb);
+    const uint32_t sum = __reduce_add_sync(peers, cv);
+    if ((peers & lt) == 0) {
+        if (mn != 0x7F800000u) atomicMin(ray_min + r.slot, mn);
+        if (sum) atomicAdd(ray_cnt + r.slot, sum);
+    }
+}
+
 // Eq. 1 for one texel slot after its rays committed: u_t = min(u, r_t) (the
 // alpha decay was applied by the mask stage), counts += this frame's hits
 // (saturating at 16 bits), f_t = +-u_t or c_t while no ray has hit; the
@@ -357,9 +390,27 @@ __device__ __forceinline__ void finalize_slot(const TraceArgs& a, uint64_t s) {
     const uint32_t pq = __umulhi(parent, a.nc_mag), pz = __umulhi(pq, a.nc_mag);
     const uint32_t px = parent - pq * nc, py = pq - pz * nc;
     const uint32_t texel = (2 * px + (ch & 1)) + nf * ((2 * py + ((ch >> 1) & 1)) + nf * (2 * pz + (ch >> 2)));
+    if (a.nearest) {
+        // Eq. 1's minimum over (u, this frame's nearest hit), keeping the face
+        // of the smaller one (counts holds the face: 1 = back)
+        const uint32_t km = a.ray_min[s];
+        a.ray_min[s] = ray_min_none(true);
+        const float u0 = a.accum[texel];
+        const uint32_t kp = u0 == CUDART_INF_F ? 0xFFFFFFFFu : ((__float_as_uint(u0) << 1) | (a.counts[texel] & 1u));
+        const uint32_t k = min(kp, km);
+        if (k == 0xFFFFFFFFu) {
+            a.fine[texel] = a.coarse[parent];
+            return;
+        }
+        const float u = __uint_as_float(k >> 1);
+        a.accum[texel] = u;
+        a.counts[texel] = k & 1u;
+        a.fine[texel] = (k & 1u) ? -u : u;
+        return;
+    }
     const float rmin = __uint_as_float(a.ray_min[s]);
     const uint32_t cv = a.ray_cnt[s];
-    a.ray_min[s] = 0x7F800000u;
+    a.ray_min[s] = ray_min_none(false);
     a.ray_cnt[s] = 0u;
     const float u = fminf(a.accum[texel], rmin);
     const uint32_t cw = a.counts[texel];

@@ -100,3 +100,32 @@ def test_batch_barrier_timeout_reported_then_recovers():
         for k in ("seeds", "accum", "counts", "fine"):
             assert np.array_equal(got[k], ref[i][k]), (i, k)
     b.close()
+
+
+def test_batch_nearest_face_variant_equals_sequential():
+    # scenes in the nearest-face mode (and one left in the vote mode) give the
+    # grids of plain per-scene frames in the same modes
+    items = _workload()
+    d, R, frames = 2.0, 8, [0, 1, 2]
+    b = _make_batch(items)
+    for i, sc in enumerate(b.scenes):
+        if i != 2:
+            sc.set_sign_mode("nearest")
+    for f in frames:
+        b.frame(d, R, f)
+    b.sync()
+    from paper_2210_04449_gb300 import RTSDF
+    for i, ((cfg, mesh), sc) in enumerate(zip(items, b.scenes)):
+        rt = RTSDF(**cfg)
+        if i != 2:
+            rt.set_sign_mode("nearest")
+        rt.upload_mesh(mesh.verts, mesh.tris)
+        rt.build_bvh()
+        for f in frames:
+            rt.update(d, R, f)
+        rt.sync()
+        want, got = _grids(rt), _grids(sc)
+        for k in ("accum", "counts", "fine", "masked"):
+            assert np.array_equal(got[k], want[k]), (i, k)
+        rt.close()
+    b.close()

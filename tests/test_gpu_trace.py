@@ -156,3 +156,108 @@ def test_checkpoint_resume_is_bit_identical():
     ga, gb = a.grids(), b.grids()
     for k in ("accum", "counts", "fine"):
         assert np.array_equal(ga[k].cpu().numpy(), gb[k].cpu().numpy()), k
+
+
+# --------------------------------------------------------------------------
+# The nearest-face sign variant (rays capped at the texel's running minimum)
+# --------------------------------------------------------------------------
+
+def _compare_nearest(rt, pipe, label):
+    g = rt.grids()
+    tx = pipe.texels()
+    u = g["accum"].cpu().numpy().astype(np.float64)[tx]
+    back = g["counts"].cpu().numpy().astype(np.int64)[tx]
+    f = g["fine"].cpu().numpy().astype(np.float64)[tx]
+    both_inf = np.isinf(u) & np.isinf(pipe.u)
+    with np.errstate(invalid="ignore"):
+        du = np.where(both_inf, 0.0, np.abs(u - pipe.u))
+    fin = np.isfinite(pipe.u)
+    bad = (du > TOL) | (fin & (back != pipe.back)) | (np.abs(f - pipe.f) > TOL)
+    exact = np.mean((u == pipe.u) | both_inf)
+    print(f"{label}: texels={tx.size} mismatched={bad.sum()} u-exact={exact:.6f}")
+    assert bad.mean() <= 1e-4, (label, bad.sum())
+
+
+@pytest.mark.parametrize("R", [4, 16])
+def test_nearest_face_variant_matches_oracle(R):
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.tiny_scene()
+    nc, d, beta = 32, 2.0, 0.5
+    rt = RTSDF(nc, beta_vox=beta, seed=0)
+    rt.set_sign_mode("nearest")
+    assert rt.get_sign_mode() == "nearest"
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 0, sign="nearest")
+    for t in range(3):
+        rt.update(d, R, t)
+        pipe.frame(m.verts, m.tris, t, R)
+    rt.sync()
+    _compare_nearest(rt, pipe, f"nearest R={R}")
+
+
+def test_nearest_face_variant_with_motion_and_reset():
+    from paper_2210_04449_gb300 import RTSDF
+    mesh = S.animated_scene(4, n_objects=12, n_lon=16, n_lat=9)
+    nc, d, beta, R = 32, 2.0, 0.5, 8
+    rt = RTSDF(nc, beta_vox=beta, seed=9)
+    rt.set_sign_mode("nearest")
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.set_objects(mesh.vert_object, mesh.n_objects)
+    rt.build_bvh()
+    verts = mesh.verts.copy()
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 9, sign="nearest")
+    moved = None
+    for t in range(4):
+        if t > 0:
+            tr = S.object_translations(4, t, mesh.n_objects, 0.5 / nc)
+            tr[::3] = 0.0
+            lo = np.stack([verts[mesh.vert_object == k].min(0) for k in range(mesh.n_objects)])
+            hi = np.stack([verts[mesh.vert_object == k].max(0) for k in range(mesh.n_objects)])
+            mv = np.any(tr != 0, axis=1)
+            moved = (lo[mv], hi[mv])
+            verts = (verts + tr[mesh.vert_object]).astype(np.float32)
+            rt.move_objects(tr)
+            rt.build_bvh(refit=True)
+        rt.update(d, R, t)
+        pipe.frame(verts, mesh.tris, t, R, moved_aabbs=moved)
+    rt.sync()
+    _compare_nearest(rt, pipe, "nearest motion")
+
+
+def test_nearest_face_keeps_the_vote_distances_and_mode_rules():
+    from paper_2210_04449_gb300 import RTSDF, RtsdfError
+    m = S.room_scene(2, n_objects=20, n_spheres=8, subdiv=2)
+    nc, d, R = 48, 2.0, 8
+    a = RTSDF(nc, seed=5)
+    b = RTSDF(nc, seed=5)
+    b.set_sign_mode("nearest")
+    for rt in (a, b):
+        rt.upload_mesh(m.verts, m.tris)
+        rt.build_bvh()
+    for t in range(3):
+        a.update(d, R, t)
+        b.update(d, R, t)
+    ga, gb = a.grids(), b.grids()
+    # the same rays find the same minimum: capped rays lose nothing
+    assert np.array_equal(ga["accum"].cpu().numpy(), gb["accum"].cpu().numpy())
+    # the state records its mode; loading it adopts the mode
+    state = b.save_state()
+    c = RTSDF(nc, seed=5)
+    c.upload_mesh(m.verts, m.tris)
+    c.build_bvh()
+    c.load_state(state)
+    assert c.get_sign_mode() == "nearest"
+    for rt in (b, c):
+        rt.update(d, R, 3)
+    for k in ("accum", "counts", "fine"):
+        assert np.array_equal(b.grids()[k].cpu().numpy(), c.grids()[k].cpu().numpy()), k
+    # switching the mode restarts the accumulation
+    c.set_sign_mode("vote")
+    assert np.all(np.isinf(c.grids()["accum"].cpu().numpy()))
+    from paper_2210_04449_gb300.context import call
+    with pytest.raises(RtsdfError):
+        call("rtsdf_set_sign_mode", c._h, 7)     # unknown mode
+    for rt in (a, b, c):
+        rt.sync()
+        rt.close()
