@@ -63,6 +63,24 @@ def _src_hash(*names):
     return h.hexdigest()[:16]
 
 
+def reduce_max(x, world, device=None):
+    """Largest value of x over the ranks (every rank gets it): replicas are
+    timed by the slowest one.  Any torch.distributed backend: pass a CUDA
+    device for NCCL, None for gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_frame(ms_frame_slowest, world):
+    """Whole-job ms per frame of `world` replicas that each run one frame per
+    step: world frames every ms_frame_slowest."""
+    return ms_frame_slowest / max(int(world), 1)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,10 +211,7 @@ def run_gpu(args, rank, world):
     launches = st["launches"] - launches0
     rt.sync()
     n_masked_tex = st["n_masked_texels"]
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = reduce_max(ms_total, world, dev)
     ms_frame = ms_total / args.steps
     stage = {k: (v / args.steps if st["stage_calls"][k] else None) for k, v in st["stage_ms"].items()}
 
@@ -214,13 +229,14 @@ def run_gpu(args, rank, world):
     trans_host = torch.tensor(trans, dtype=torch.float32).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize(dev)
+    barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         t = tnext + 1 + i
         frame(t, trans_host[(t % n_frames) or 1])
         rt.masked_count()
         rt.sync()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms = reduce_max((time.perf_counter() - t0) * 1e3 / e2e_steps, world, dev)
 
     # Sec. 2.3 on the frame's fine SDF: 1920x1080 floor points, one light,
     # k = 8, 64 steps (forward) and the adjoint at 1024x1024
@@ -254,7 +270,7 @@ def run_gpu(args, rank, world):
 
     line = {
         "metric": METRIC,
-        "value": round(ms_frame / world, 3),
+        "value": round(job_ms_per_frame(ms_frame, world), 3),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -294,7 +310,7 @@ def run_gpu(args, rank, world):
                      "traffic": traffic,
                      "peak_source": f"derived: {sms} SMs x 128 fp32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"},
         "clocks": clk,
-        "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": N_OBJ * 3 * 4,
+        "e2e": {"value": round(job_ms_per_frame(e2e_ms, world), 3), "unit": UNIT, "h2d_bytes_per_step": N_OBJ * 3 * 4,
                 "d2h_bytes_per_step": 8 + 4},
         "shadow": shadow,
         "tuning": tuning,
