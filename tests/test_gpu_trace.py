@@ -107,6 +107,40 @@ def test_room_sampled_texels():
     _compare(rt, pipe, sample, "room sample")
 
 
+def test_full_size_animated_frames_sampled_texels():
+    # the benchmark workload: 500 displaced spheres (1,000,000 triangles),
+    # 256^3 -> 512^3, 64 rays per texel, every object moved before the second
+    # frame (refit, re-voxelize, JFA, reset), in the autotuned launch
+    # configuration the benchmark times; 96 fine texels sampled from the
+    # masked ones are traced by the oracle by brute force over all triangles
+    from paper_2210_04449_gb300 import RTSDF
+    mesh = S.animated_scene(2, n_objects=500)
+    nc, d, beta, R, seed = 256, 2.0, 0.5, 64, 2
+    rt = RTSDF(nc, beta_vox=beta, seed=seed)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.set_objects(mesh.vert_object, mesh.n_objects)
+    rt.build_bvh()
+    rt.update(d, R, 0)
+    rt.autotune(d, R, 1, use_cache=True)          # saves and restores the state
+    n_m = rt.masked_count()
+    masked = rt.grids()["masked"].cpu().numpy()[:n_m]
+    sample = np.sort(np.random.default_rng(12).choice(child_texels(masked, nc), 96, replace=False))
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, seed, track=sample)
+    pipe.frame(mesh.verts, mesh.tris, 0, R)
+    tr = S.object_translations(seed, 1, mesh.n_objects, 0.5 / nc)
+    lo = np.stack([mesh.verts[mesh.vert_object == k].min(0) for k in range(mesh.n_objects)])
+    hi = np.stack([mesh.verts[mesh.vert_object == k].max(0) for k in range(mesh.n_objects)])
+    mv = np.any(tr != 0, axis=1)
+    verts1 = (mesh.verts + tr[mesh.vert_object]).astype(np.float32)
+    rt.move_objects(tr)
+    rt.build_bvh(refit=True)
+    rt.update(d, R, 1)
+    pipe.frame(verts1, mesh.tris, 1, R, moved_aabbs=(lo[mv], hi[mv]))
+    rt.sync()
+    exact = _compare(rt, pipe, sample, "animated 1M full size sample")
+    assert exact == 1.0
+
+
 def test_motion_refit_and_reset():
     from paper_2210_04449_gb300 import RTSDF
     mesh = S.animated_scene(4, n_objects=12, n_lon=16, n_lat=9)
