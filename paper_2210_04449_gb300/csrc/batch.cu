@@ -38,6 +38,11 @@ namespace {
 using namespace dev;
 
 constexpr int MAX_BATCH = 256;
+// minimum resident blocks per SM the compiler must allow (register budget
+// 65536 / (128 x this) per thread)
+#ifndef BATCH_BLOCKS_PER_SM
+#define BATCH_BLOCKS_PER_SM 8
+#endif
 constexpr uint32_t BARRIER_SPINS = 1u << 27;   // default polls (>= 64 ns each): several seconds
 
 struct SceneDesc {
@@ -180,15 +185,55 @@ __device__ __noinline__ void batch_voxelize_big(const BatchArgs& b) {
     }
 }
 
-__global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
+// Jump-flood pass p of every scene that has one, as one grid-stride loop
+// over all scenes' voxels (voxel prefix vp), so that small scenes do not
+// leave most threads idle; a thread's voxel index only grows, so its scene
+// index only moves forward.  Not inlined: the 27 candidates' registers then
+// do not shape the register allocation of the whole persistent kernel (the
+// trace stage above all).
+__device__ __noinline__ void batch_jfa_pass(const BatchArgs& b, const unsigned long long* vp, int ns, int p,
+                                            uint64_t tid, uint64_t nthr) {
+    const unsigned long long total = vp[ns];
+    int s = -1;
+    unsigned long long lo = 0, hi = 0;
+    for (unsigned long long g = tid; g < total; g += nthr) {
+        if (g >= hi) {
+            do s++;
+            while (vp[s + 1] <= g);
+            lo = vp[s];
+            hi = vp[s + 1];
+        }
+        const SceneDesc& d = b.sc[s];
+        const int L = d.passes;
+        if (p >= L) {          // this scene has no pass p: skip its voxels
+            g = hi - 1 - ((hi - 1 - g) % nthr);
+            continue;
+        }
+        const uint32_t n = (uint32_t)d.t.nc, mag = d.nmag;
+        const uint32_t v = (uint32_t)(g - lo);
+        const uint32_t vq = __umulhi(v, mag), z = __umulhi(vq, mag);
+        const int x = (int)(v - vq * n), y = (int)(vq - z * n);
+        const int k = 1 << (L - 1 - p);
+        const uint32_t* in = d.seeds[p & 1];
+        uint32_t* out = d.seeds[(p + 1) & 1];
+        float* coarse = const_cast<float*>(d.t.coarse);
+        if (p == L - 1) jfa_voxel<true, false>(in, out, (int)n, k, x, y, (int)z, coarse, d.hc, d.beta_h);
+        else jfa_voxel<false, false>(in, out, (int)n, k, x, y, (int)z, coarse, d.hc, d.beta_h);
+    }
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_frame(BatchArgs b) {
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint64_t nthr = gridDim.x * (uint64_t)blockDim.x;
-    const BatchParams P = *b.params;
+    // the frame's parameters live in shared memory, not in registers that
+    // would stay allocated through the trace stage
+    __shared__ BatchParams P;
     const int ns = b.ns;
     stamp(b, 0);
     // prefix over scenes: voxels in stages 0-4, rays in stages 5-6
     __shared__ unsigned long long s_prefix[MAX_BATCH + 1];
     unsigned long long* s_vp = s_prefix;
+    if (threadIdx.x == 0) P = *b.params;
     for (int i = threadIdx.x; i <= ns; i += blockDim.x) s_vp[i] = b.vox_prefix[i];
     __syncthreads();
 
@@ -218,24 +263,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
 
     // ---- stage 3: jump flooding, pass p of every scene that has one
     for (int p = 0; p < b.max_passes; p++) {
-        for (int s = 0; s < ns; s++) {
-            const SceneDesc& d = b.sc[s];
-            const int L = d.passes;
-            if (p >= L) continue;
-            const uint32_t n = (uint32_t)d.t.nc, mag = d.nmag, n3 = n * n * n;
-            if (tid >= n3) continue;
-            const uint32_t* in = d.seeds[p & 1];
-            uint32_t* out = d.seeds[(p + 1) & 1];
-            float* coarse = const_cast<float*>(d.t.coarse);
-            const float hc = d.hc, beta_h = d.beta_h;
-            const int k = 1 << (L - 1 - p);
-            for (uint32_t v = (uint32_t)tid; v < n3; v += (uint32_t)nthr) {
-                const uint32_t vq = __umulhi(v, mag), z = __umulhi(vq, mag);
-                const int x = (int)(v - vq * n), y = (int)(vq - z * n);
-                if (p == L - 1) jfa_voxel<true, false>(in, out, (int)n, k, x, y, (int)z, coarse, hc, beta_h);
-                else jfa_voxel<false, false>(in, out, (int)n, k, x, y, (int)z, coarse, hc, beta_h);
-            }
-        }
+        batch_jfa_pass(b, s_vp, ns, p, tid, nthr);
         if (!grid_barrier(b)) return;
     }
     // scenes without jump steps (N = 1): coarse value straight from the seed
@@ -428,7 +456,11 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_batch_frame(BatchArgs b) {
         int sc = -1;
         unsigned long long lo = 0, hi = 0;   // slot range of scene sc
         TraceArgs ta;
-        for (unsigned long long g = tid; g < stot; g += nthr) {
+        // thread index and count recomputed here, so that they are not
+        // live through the trace stage
+        const unsigned long long ftid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+        const unsigned long long fnthr = gridDim.x * (unsigned long long)blockDim.x;
+        for (unsigned long long g = ftid; g < stot; g += fnthr) {
             if (g >= hi) {
                 do sc++;
                 while ((s_rp[sc + 1] >> lg) <= g);
@@ -485,9 +517,9 @@ struct rtsdf_batch {
     int max_passes = 0;
     // launch configuration (autotuned)
     int blocks_per_sm = 0;       // 0 = occupancy maximum
-    int refill_min = 16;
+    int refill_min = 12;
     int ray_chunk = 1024;
-    int leaf_min = 16;
+    int leaf_min = 12;
     int use_graph = 1;
     int barrier_spins = 0;
     unsigned grid = 0;

@@ -145,7 +145,7 @@ struct rtsdf_ctx {
 
     // launch parameters (rtsdf_set_tuning / rtsdf_autotune)
     int sign_mode = RTSDF_SIGN_VOTE;   // rtsdf_set_sign_mode
-    rtsdf_tuning tune = {0, 0, 16, 1024, 16};
+    rtsdf_tuning tune = {4, 0, 12, 1024, 12};   // the autotuner's usual pick
 
     rtsdf::Bvh bvh;
     bool bvh_dirty = true;

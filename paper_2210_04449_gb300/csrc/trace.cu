@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
         // trace until enough lanes are idle to be worth a refill
         for (;;) {
             const bool done = warp_step<COUNT>(a, r, stk, active, a.leaf_min, n_visits, n_tests, n_leaf_slots);
-            if (COUNT) n_slots++;
+            if (COUNT) n_slots += NODE_STEPS;   // lane slots of the node steps
             const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
             if (fin && done) {
                 const unsigned peers = __match_any_sync(fin, r.slot);

@@ -336,13 +336,22 @@ __device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint
 }
 
 // One warp iteration of the two-phase traversal for every lane (active or
-// not: call it convergently).  Returns true for a lane whose ray finished.
+// not: call it convergently): NODE_STEPS node steps, then the leaf phase if
+// enough lanes wait on a parked leaf.  Two node steps per iteration halve
+// the cost of the phase decision (three ballots) per node visit; measured on
+// the 1M-triangle frame: 1 step 525 ms, 2 steps 497 ms, 3 steps 517 ms,
+// 4 steps 499 ms.  Returns true for a lane whose ray finished.
+constexpr int NODE_STEPS = 2;
+
 // COUNT: visits / tests count this lane's node visits and triangle tests,
 // leaf_slots the iterations in which the warp ran its leaf phase.
 template <bool COUNT, class A>
 __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool active, int leaf_min,
                                           uint32_t& visits, uint32_t& tests, uint32_t& leaf_slots) {
-    if (active) node_step<COUNT>(a, r, stack, visits);
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < NODE_STEPS; i++) node_step<COUNT>(a, r, stack, visits);
+    }
     const bool parked = active && r.leaf != WIDE_EMPTY;
     const bool blocked = parked && r.node < 0;             // cannot go on before its leaf
     const unsigned pm = __ballot_sync(0xFFFFFFFFu, parked);
