@@ -50,8 +50,8 @@ FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 # once trace.cu or trace_dev.cuh changes.
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
-    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch" (1 pass): 7.13 GB + 179.13 MB
-    "4cb47ae20f930ad9": 7.13e9 + 179.13e6,
+    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch" (1 pass): 6.95 GB + 177.09 MB
+    "f09bb96449ddcf4e": 6.95e9 + 177.09e6,
 }
 
 
