@@ -638,7 +638,7 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
     if (to > b->tri_cap) {
         if (b->d_tri_all) cudaFree(b->d_tri_all);
         b->d_tri_all = nullptr;
-        if ((e = cudaMalloc(&b->d_tri_all, sizeof(float4) * 3 * (to > 0 ? to : 1)))) return e;
+        if ((e = cudaMalloc(&b->d_tri_all, sizeof(float4) * TRI_F4 * (to > 0 ? to : 1)))) return e;
         b->tri_cap = to;
     }
     b->total_nt = to;
@@ -651,7 +651,7 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
             b->launches++;
         }
         if (bv.nt > 0 &&
-            (e = cudaMemcpyAsync(b->d_tri_all + 3 * (int64_t)desc[s].tri_off, bv.tri, sizeof(float4) * 3 * bv.nt,
+            (e = cudaMemcpyAsync(b->d_tri_all + TRI_F4 * (int64_t)desc[s].tri_off, bv.tri, sizeof(float4) * TRI_F4 * bv.nt,
                                  cudaMemcpyDeviceToDevice, b->stream)))
             return e;
     }

@@ -199,9 +199,10 @@ __global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __re
     const float* p1 = verts + 3 * (int64_t)tris[3 * (int64_t)t + 1];
     const float* p2 = verts + 3 * (int64_t)tris[3 * (int64_t)t + 2];
     const float v0[3] = {p0[0], p0[1], p0[2]}, v1[3] = {p1[0], p1[1], p1[2]}, v2[3] = {p2[0], p2[1], p2[2]};
-    tri[3 * i + 0] = make_float4(v0[0], v0[1], v0[2], __int_as_float(t));
-    tri[3 * i + 1] = make_float4(__fsub_rn(v1[0], v0[0]), __fsub_rn(v1[1], v0[1]), __fsub_rn(v1[2], v0[2]), 0.f);
-    tri[3 * i + 2] = make_float4(__fsub_rn(v2[0], v0[0]), __fsub_rn(v2[1], v0[1]), __fsub_rn(v2[2], v0[2]), 0.f);
+    tri[TRI_F4 * i + 0] = make_float4(v0[0], v0[1], v0[2], __int_as_float(t));
+    tri[TRI_F4 * i + 1] = make_float4(__fsub_rn(v1[0], v0[0]), __fsub_rn(v1[1], v0[1]), __fsub_rn(v1[2], v0[2]), 0.f);
+    tri[TRI_F4 * i + 2] = make_float4(__fsub_rn(v2[0], v0[0]), __fsub_rn(v2[1], v0[1]), __fsub_rn(v2[2], v0[2]), 0.f);
+    tri[TRI_F4 * i + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
     leaf_tri[i] = t;
     if (n == 1) return;
     float lo[3], hi[3];
@@ -414,7 +415,7 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     };
     const int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
     if ((e = realloc_if((void**)&b.nodes, sizeof(BNode) * (size_t)(n > 1 ? n - 1 : 1)))) return e;
-    if ((e = realloc_if((void**)&b.tri, sizeof(float4) * 3 * (size_t)n))) return e;
+    if ((e = realloc_if((void**)&b.tri, sizeof(float4) * TRI_F4 * (size_t)n))) return e;
     if ((e = realloc_if((void**)&b.leaf_tri, sizeof(int32_t) * (size_t)n))) return e;
     if ((e = realloc_if((void**)&b.leaf_parent, sizeof(int32_t) * (size_t)n))) return e;
     if ((e = realloc_if((void**)&b.flags, sizeof(uint32_t) * (size_t)n))) return e;

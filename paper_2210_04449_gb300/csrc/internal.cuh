@@ -43,6 +43,9 @@ struct __align__(16) BNode {
 // binary source of every child (>= 0 binary node, < 0 ~leaf, WIDE_EMPTY = no
 // child; an empty slot has lo = +inf, hi = -inf and never hits).  128 bytes,
 // 32-byte aligned: each (lo, hi) pair of an axis is one 32-byte sector.
+// Leaf triangles: (v0, original index), e1, e2 as float4 and one float4 of
+// padding, so that each triangle is two aligned 32-byte sectors.
+constexpr int TRI_F4 = 4;
 constexpr int WIDE_EMPTY = (int)0x80000000;
 struct __align__(32) WNode {
     float4 lox, hix, loy, hiy, loz, hiz;

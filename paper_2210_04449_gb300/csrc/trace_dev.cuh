@@ -317,9 +317,10 @@ __device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint
         visits++;
         tests++;
     }
-    const float4 p0 = __ldg(&a.tri[3 * leaf]);
-    const float4 p1 = __ldg(&a.tri[3 * leaf + 1]);
-    const float4 p2 = __ldg(&a.tri[3 * leaf + 2]);
+    // one triangle = two aligned 32-byte sectors (v0 | index, e1) and (e2, pad)
+    float4 p0, p1, p2, pad;
+    ldg256(&a.tri[TRI_F4 * leaf], p0, p1);
+    ldg256(&a.tri[TRI_F4 * leaf + 2], p2, pad);
     float t;
     bool fr;
     if (ray_tri(r.o, r.d, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
