@@ -17,12 +17,16 @@
 //     distances keep the smaller original triangle index.
 // Rays of very different lengths would leave most lanes of a lock-step warp
 // idle, so warps are persistent and refill idle lanes with new ray ids from
-// a warp-local chunk.  A finished ray commits its distance (atomicMin on the
+// a warp-local chunk once enough lanes are idle.  The traversal runs in two
+// phases (a lane parks the leaf it reaches and keeps descending; the warp
+// tests triangles when enough lanes hold a parked leaf), two node steps per
+// phase decision.  A finished ray commits its distance (atomicMin on the
 // float bits, t >= 0) and its front/back hit into per-slot scratch with
 // warp-aggregated atomics; k_trace_finalize then applies Eq. 1 per texel:
 // u_t = min(u, r_t) (the alpha decay was applied by the mask kernel), the
 // counts, and f_t = +-u_t (c_t while no ray has hit), negative when back
-// hits outnumber front hits.
+// hits outnumber front hits.  In the nearest-face sign mode a ray starts
+// with the texel's u as its best hit and commits (t, face) as one key.
 #include <math_constants.h>
 
 #include "internal.cuh"
