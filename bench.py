@@ -50,8 +50,9 @@ FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 # once trace.cu or trace_dev.cuh changes.
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
-    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch" (1 pass): 6.95 GB + 177.09 MB
-    "f09bb96449ddcf4e": 6.95e9 + 177.09e6,
+    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant" (1 pass):
+    # 12.08 GB + 177.08 MB
+    "e7380462910d1162": 12.08e9 + 177.08e6,
 }
 
 
