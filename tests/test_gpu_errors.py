@@ -1,0 +1,131 @@
+"""Error behaviour of the C ABI with a GPU: bad meshes (E_MESH), calls out
+of order (E_STATE), bad arguments (E_ARG), and that a context is usable
+again after each.  Nothing here provokes a device fault: every error is a
+host-side argument check or a device validation word (bad indices are
+rewritten to 0 and bad vertices clamped before any kernel reads them)."""
+import numpy as np
+import pytest
+
+from synth import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _name(fn, *a, **k):
+    from paper_2210_04449_gb300 import RtsdfError
+    with pytest.raises(RtsdfError) as ei:
+        fn(*a, **k)
+    return ei.value.name
+
+
+def _fine_after_frame(rt, m, d=2.0, R=8):
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    rt.update(d, R, 0)
+    rt.sync()
+    return rt.grids()["fine"].cpu().numpy().copy()
+
+
+def test_mesh_validation_then_recovery():
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.tiny_scene()
+    rt = RTSDF(16, seed=1)
+    bad_index = m.tris.copy()
+    bad_index[5, 1] = m.verts.shape[0]                  # one past the last vertex
+    assert _name(rt.upload_mesh, m.verts, bad_index) == "RTSDF_E_MESH"
+    negative = m.tris.copy()
+    negative[0, 0] = -1
+    assert _name(rt.upload_mesh, m.verts, negative) == "RTSDF_E_MESH"
+    nan_vert = m.verts.copy()
+    nan_vert[3, 0] = np.nan
+    assert _name(rt.upload_mesh, nan_vert, m.tris) == "RTSDF_E_MESH"
+    far_vert = m.verts.copy()
+    far_vert[0] = (5.0, 5.0, 5.0)                       # outside [bmin - E/2, bmin + 3E/2]
+    assert _name(rt.upload_mesh, far_vert, m.tris) == "RTSDF_E_MESH"
+    # a rejected mesh leaves the context without a mesh
+    assert _name(rt.voxelize) == "RTSDF_E_STATE"
+    assert _name(rt.build_bvh) == "RTSDF_E_STATE"
+    # a valid mesh afterwards gives exactly a fresh context's result
+    got = _fine_after_frame(rt, m)
+    want = _fine_after_frame(RTSDF(16, seed=1), m)
+    assert np.array_equal(got, want)
+    rt.close()
+
+
+def test_calls_out_of_order():
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.animated_scene(3, n_objects=4, n_lon=12, n_lat=7)
+    rt = RTSDF(16)
+    assert _name(rt.voxelize) == "RTSDF_E_STATE"         # no mesh yet
+    rt.upload_mesh(m.verts, m.tris)
+    assert _name(rt.jfa) == "RTSDF_E_STATE"              # before voxelize
+    assert _name(rt.build_bvh, refit=True) == "RTSDF_E_STATE"   # refit before a build
+    assert _name(rt.trace, 2.0, 8, 0) == "RTSDF_E_STATE"         # before jfa
+    assert _name(rt.move_objects, np.zeros((4, 3), np.float32)) == "RTSDF_E_STATE"   # no objects
+    rt.voxelize()
+    rt.jfa()
+    assert _name(rt.trace, 2.0, 8, 0) == "RTSDF_E_STATE"         # no BVH yet
+    rt.set_objects(m.vert_object, m.n_objects)
+    rt.build_bvh()
+    rt.trace(2.0, 8, 0)
+    rt.move_objects(np.full((4, 3), 0.01, np.float32))
+    assert _name(rt.trace, 2.0, 8, 1) == "RTSDF_E_STATE"         # moved: the BVH needs a refit
+    rt.build_bvh(refit=True)
+    rt.update(2.0, 8, 1)
+    rt.sync()
+    rt.close()
+
+
+def test_argument_checks():
+    import torch
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.tiny_scene()
+    rt = RTSDF(16)
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    rt.voxelize()
+    rt.jfa()
+    for rays in (0, 3, 2048):
+        assert _name(rt.trace, 2.0, rays, 0) == "RTSDF_E_ARG"
+    assert _name(rt.trace, float("nan"), 8, 0) == "RTSDF_E_ARG"
+    assert _name(rt.trace, 2.0, 8, -1) == "RTSDF_E_ARG"
+    rt.trace(2.0, 1, 0)                                   # the extremes of the ray count are valid
+    rt.trace(2.0, 1024, 1)
+    pos, nrm = S.floor_gbuffer(8, 8, y=0.05)
+    tp, tn = torch.tensor(pos, device=rt.device), torch.tensor(nrm, device=rt.device)
+    assert _name(rt.shadow, tp, tn, (0.4, 1.0, 0.3), steps=0) == "RTSDF_E_ARG"
+    assert _name(rt.shadow, tp, tn, (0.4, 1.0, 0.3), steps=257) == "RTSDF_E_ARG"
+    assert _name(rt.shadow, tp, tn, (0.4, 1.0, 0.3), k=0.0) == "RTSDF_E_ARG"
+    assert _name(rt.shadow, tp, tn, (0.0, 0.0, 0.0)) == "RTSDF_E_ARG"
+    assert _name(rt.shadow, tp, tn, (0.4, 1.0, 0.3), jitter_vox=-1.0) == "RTSDF_E_ARG"
+    img = torch.zeros((8, 8), device=rt.device)
+    assert _name(rt.taa_resolve, img, img, 0.1) == "RTSDF_E_ARG"           # cur and hist overlap
+    assert _name(rt.taa_resolve, img.clone(), img, 0.0) == "RTSDF_E_ARG"   # blend outside (0, 1]
+    assert _name(rt.set_tuning, refill_min=0) == "RTSDF_E_ARG"
+    assert _name(rt.set_tuning, jfa_tile=9) == "RTSDF_E_ARG"
+    state = rt.save_state()
+    assert _name(rt.load_state, state[:-1]) == "RTSDF_E_ARG"              # truncated
+    other = RTSDF(8)
+    assert _name(other.load_state, state) == "RTSDF_E_ARG"                # another grid size
+    rt.sync()
+    other.close()
+    rt.close()
+
+
+def test_motion_leaving_the_volume_is_reported_and_cleared():
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.animated_scene(5, n_objects=3, n_lon=12, n_lat=7)
+    rt = RTSDF(16)
+    rt.upload_mesh(m.verts, m.tris)
+    rt.set_objects(m.vert_object, m.n_objects)
+    rt.build_bvh()
+    rt.update(2.0, 4, 0)
+    rt.sync()
+    far = np.zeros((3, 3), np.float32)
+    far[1] = (10.0, 0.0, 0.0)                             # object 1 leaves the accepted box
+    rt.move_objects(far)
+    rt.build_bvh(refit=True)
+    rt.update(2.0, 4, 1)
+    assert _name(rt.sync) == "RTSDF_E_MESH"               # clamped, reported once
+    rt.sync()                                             # the status word was cleared
+    rt.close()
