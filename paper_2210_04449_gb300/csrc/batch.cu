@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
         int2 deep[TRACE_STACK - SMEM_STACK];
         Stack stk{&s_stack[0][threadIdx.x], deep};
         Ray r;
-        int scene = 0;
+        __shared__ int s_scene[TRACE_THREADS];   // scene of each lane's ray (read only at setup and commit)
         bool active = false;
         bool exhausted = false;
         uint32_t dummy_v = 0, dummy_t = 0, dummy_l = 0;
@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
                     const uint32_t rank = __popc(idle & lt);
                     if (rank < take) {
                         const unsigned long long g = cn + rank;
-                        scene = g < s_csend[wi] ? s_cscene[wi] : find_scene(s_rp, ns, g);
+                        const int scene = g < s_csend[wi] ? s_cscene[wi] : find_scene(s_rp, ns, g);
+                        s_scene[threadIdx.x] = scene;
                         TraceArgs ta = b.sc[scene].t;
                         ta.rays = P.rays;
                         ta.log2_rays = P.log2_rays;
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
                 const bool done = warp_step<false>(b.bvh, r, stk, active, b.leaf_min, dummy_v, dummy_t, dummy_l);
                 const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
                 if (fin && done) {
+                    const int scene = s_scene[threadIdx.x];
                     const unsigned long long key = ((unsigned long long)scene << 32) | r.slot;
                     const unsigned peers = __match_any_sync(fin, key);
                     const TraceArgs& st = b.sc[scene].t;
