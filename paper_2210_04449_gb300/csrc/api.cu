@@ -77,6 +77,8 @@ void free_all(rtsdf_ctx* c) {
     dfree(c->ray_min); dfree(c->ray_cnt); dfree(c->d_next_ray);
     dfree(c->bin_count); dfree(c->bin_start); dfree(c->bin_cursor); dfree(c->bin_items); dfree(c->bin_overflow);
     dfree(c->bvh.nodes); dfree(c->bvh.wide); dfree(c->bvh.nbox); dfree(c->bvh.lbox); dfree(c->bvh.tri); dfree(c->bvh.leaf_tri); dfree(c->bvh.leaf_parent); dfree(c->bvh.flags);
+    dfree(c->bvh.col_fb); dfree(c->bvh.col_fslot); dfree(c->bvh.col_nb); dfree(c->bvh.col_nslot);
+    dfree(c->bvh.col_kids); dfree(c->bvh.col_nint); dfree(c->bvh.col_total);
     dfree(c->d_err);
     dfree(c->d_counters);
     for (auto& t : c->timers) {

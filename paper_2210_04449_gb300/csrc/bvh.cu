@@ -323,76 +323,141 @@ __global__ void k_translate(float* __restrict__ verts, const int32_t* __restrict
 
 }  // namespace
 
-// Collapse the binary tree into 4-wide nodes (host side, once per build):
-// starting from a binary node's two children, the internal child with the
-// largest surface area is replaced by its two children until four are
-// collected (or only leaves remain); each internal child becomes a wide node.
-static cudaError_t collapse_wide(rtsdf_ctx* c) {
-    Bvh& b = c->bvh;
-    const int64_t n = b.nt;
-    std::vector<BNode> bn((size_t)(n - 1));
-    std::vector<float> box((size_t)(n - 1) * 6);
-    cudaError_t e = cudaMemcpyAsync(bn.data(), b.nodes, sizeof(BNode) * (n - 1), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(box.data(), b.nbox, sizeof(float) * 6 * (n - 1), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return e;
-    auto area = [&](int node) {
-        const float* p = &box[6 * (size_t)node];
-        const float dx = p[3] - p[0], dy = p[4] - p[1], dz = p[5] - p[2];
-        return dx * dy + dy * dz + dz * dx;
-    };
-    std::vector<WNode> wide;
-    wide.reserve((size_t)(n / 2 + 1));
-    std::vector<std::pair<int, int>> todo;   // (binary node, wide slot)
-    wide.emplace_back();
-    todo.emplace_back(0, 0);
-    for (size_t q = 0; q < todo.size(); q++) {
-        const int bnode = todo[q].first, w = todo[q].second;
-        int kids[4] = {bn[bnode].d.x, bn[bnode].d.y, 0, 0};
-        int nk = 2;
-        while (nk < 4) {
-            int best = -1;
-            float ba = -1.f;
-            for (int k = 0; k < nk; k++)
-                if (kids[k] >= 0 && area(kids[k]) > ba) {
-                    ba = area(kids[k]);
+// Collapse the binary tree into 4-wide nodes, on the device, one tree level
+// at a time: every frontier node (a binary node that roots a wide node)
+// starts from its two children and replaces the internal child of largest
+// surface area by its two children until four are collected (or only
+// leaves remain); each internal child roots a wide node of the next level.
+// Slots are handed out in frontier order by an exclusive scan of the
+// internal-child counts, so the layout is breadth-first with the children
+// of a node contiguous.
+namespace {
+
+__device__ __forceinline__ float half_area(const float* __restrict__ nbox, int node) {
+    const float* p = nbox + 6 * (int64_t)node;
+    const float dx = p[3] - p[0], dy = p[4] - p[1], dz = p[5] - p[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_collapse_expand(const int32_t* __restrict__ fb, int32_t cnt, const BNode* __restrict__ bn,
+                                  const float* __restrict__ nbox, int4* __restrict__ kids,
+                                  uint32_t* __restrict__ nint) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int4 d = bn[fb[i]].d;
+    int kid[4] = {d.x, d.y, WIDE_EMPTY, WIDE_EMPTY};
+    int nk = 2;
+    while (nk < 4) {
+        int best = -1;
+        float ba = -1.f;
+        for (int k = 0; k < nk; k++)
+            if (kid[k] >= 0) {
+                const float ar = half_area(nbox, kid[k]);
+                if (ar > ba) {
+                    ba = ar;
                     best = k;
                 }
-            if (best < 0) break;
-            const int open = kids[best];
-            kids[best] = bn[open].d.x;
-            kids[nk++] = bn[open].d.y;
-        }
-        int child[4], src[4];
-        for (int k = 0; k < 4; k++) {
-            if (k >= nk) {
-                child[k] = WIDE_EMPTY;
-                src[k] = WIDE_EMPTY;
+            }
+        if (best < 0) break;
+        const int4 od = bn[kid[best]].d;
+        kid[best] = od.x;
+        kid[nk++] = od.y;
+    }
+    kids[i] = make_int4(kid[0], kid[1], kid[2], kid[3]);
+    nint[i] = (kid[0] >= 0) + (kid[1] >= 0) + (kid[2] >= 0) + (kid[3] >= 0);
+}
+
+__global__ void k_collapse_write(const int32_t* __restrict__ fslot, int32_t cnt, const int4* __restrict__ kids,
+                                 const uint32_t* __restrict__ off, int32_t base, int64_t cap, WNode* __restrict__ wide,
+                                 int32_t* __restrict__ nb, int32_t* __restrict__ nslot, int32_t* __restrict__ total) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int4 kv = kids[i];
+    const int kid[4] = {kv.x, kv.y, kv.z, kv.w};
+    const uint32_t o = off[i];
+    uint32_t j = 0;
+    int child[4], src[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        src[k] = kid[k];
+        if (kid[k] == WIDE_EMPTY) {
+            child[k] = WIDE_EMPTY;
+        } else if (kid[k] >= 0) {
+            const int32_t slot = base + (int32_t)(o + j);
+            if ((int64_t)slot >= cap) {   // only a damaged tree gets here: drop the child, the host stops
+                child[k] = src[k] = WIDE_EMPTY;
+                j++;
                 continue;
             }
-            src[k] = kids[k];
-            if (kids[k] >= 0) {
-                child[k] = (int)wide.size();
-                wide.emplace_back();
-                todo.emplace_back(kids[k], child[k]);
-            } else {
-                child[k] = kids[k];   // ~leaf
-            }
+            child[k] = slot;
+            nb[o + j] = kid[k];
+            nslot[o + j] = slot;
+            j++;
+        } else {
+            child[k] = kid[k];   // ~leaf
         }
-        wide[(size_t)w].child = make_int4(child[0], child[1], child[2], child[3]);
-        wide[(size_t)w].src = make_int4(src[0], src[1], src[2], src[3]);
     }
-    if (b.wide) cudaFree(b.wide);
-    b.wide = nullptr;
-    b.n_wide = (int64_t)wide.size();
-    if ((e = cudaMalloc(&b.wide, sizeof(WNode) * wide.size()))) return e;
-    if ((e = cudaMemcpyAsync(b.wide, wide.data(), sizeof(WNode) * wide.size(), cudaMemcpyHostToDevice, c->stream)))
-        return e;
+    const int32_t w = fslot[i];
+    wide[w].child = make_int4(child[0], child[1], child[2], child[3]);
+    wide[w].src = make_int4(src[0], src[1], src[2], src[3]);
+    if (i == cnt - 1) *total = (int32_t)(o + j);
+}
+
+__global__ void k_collapse_root(int32_t* fb, int32_t* fslot) {
+    fb[0] = 0;
+    fslot[0] = 0;
+}
+
+}  // namespace
+
+static cudaError_t collapse_wide(rtsdf_ctx* c) {
+    Bvh& b = c->bvh;
+    const int64_t n = b.nt;                  // n >= 2: n - 1 binary internal nodes
+    const int64_t cap = n - 1;               // every wide node roots a distinct binary node
+    cudaError_t e;
+    if (b.col_cap < cap) {
+        cudaFree(b.col_fb); cudaFree(b.col_fslot); cudaFree(b.col_nb); cudaFree(b.col_nslot);
+        cudaFree(b.col_kids); cudaFree(b.col_nint); cudaFree(b.col_total);
+        b.col_fb = b.col_fslot = b.col_nb = b.col_nslot = b.col_total = nullptr;
+        b.col_kids = nullptr;
+        b.col_nint = nullptr;
+        b.col_cap = 0;
+        if ((e = cudaMalloc(&b.col_fb, sizeof(int32_t) * cap)) || (e = cudaMalloc(&b.col_fslot, sizeof(int32_t) * cap)) ||
+            (e = cudaMalloc(&b.col_nb, sizeof(int32_t) * cap)) || (e = cudaMalloc(&b.col_nslot, sizeof(int32_t) * cap)) ||
+            (e = cudaMalloc(&b.col_kids, sizeof(int4) * cap)) || (e = cudaMalloc(&b.col_nint, sizeof(uint32_t) * cap)) ||
+            (e = cudaMalloc(&b.col_total, sizeof(int32_t))))
+            return e;
+        b.col_cap = cap;
+    }
+    if (b.wide_cap < cap) {
+        if (b.wide) cudaFree(b.wide);
+        b.wide = nullptr;
+        b.wide_cap = 0;
+        if ((e = cudaMalloc(&b.wide, sizeof(WNode) * cap))) return e;
+        b.wide_cap = cap;
+    }
+    int32_t *fb = b.col_fb, *fs = b.col_fslot, *nb = b.col_nb, *ns = b.col_nslot;
+    RTSDF_LAUNCH(c, k_collapse_root, 1, 1, 0, fb, fs);
+    int32_t base = 1, cnt = 1;
+    while (cnt > 0) {
+        const unsigned g = (unsigned)((cnt + 255) / 256);
+        RTSDF_LAUNCH(c, k_collapse_expand, g, 256, 0, fb, cnt, b.nodes, b.nbox, b.col_kids, b.col_nint);
+        RTSDF_LAUNCH(c, k_scan, 1, 1024, 0, b.col_nint, (int64_t)cnt);
+        RTSDF_LAUNCH(c, k_collapse_write, g, 256, 0, fs, cnt, b.col_kids, b.col_nint, base, cap, b.wide, nb, ns,
+                     b.col_total);
+        int32_t next = 0;
+        e = cudaMemcpyAsync(&next, b.col_total, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return e;
+        if (next < 0 || (int64_t)base + next > cap) return cudaErrorUnknown;   // only a damaged tree gets here
+        base += next;
+        cnt = next;
+        int32_t* t = fb; fb = nb; nb = t;
+        t = fs; fs = ns; ns = t;
+    }
+    b.n_wide = base;
     RTSDF_LAUNCH(c, k_wide_boxes, (unsigned)((4 * b.n_wide + 255) / 256), 256, 0, b.wide, b.n_wide, b.nbox, b.lbox);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
-    return e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bvh_build(rtsdf_ctx* c) {

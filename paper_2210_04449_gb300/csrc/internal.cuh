@@ -57,7 +57,14 @@ static_assert(sizeof(WNode) == 128, "4-wide node is 128 bytes");
 struct Bvh {
     int64_t nt = 0;
     BNode* nodes = nullptr;        // [nt - 1]
-    WNode* wide = nullptr;         // [n_wide]
+    WNode* wide = nullptr;         // [n_wide] (capacity wide_cap = nt - 1)
+    int64_t wide_cap = 0;
+    // device collapse scratch: frontier (binary node, wide slot) x 2, kids, counts
+    int32_t *col_fb = nullptr, *col_fslot = nullptr, *col_nb = nullptr, *col_nslot = nullptr;
+    int4* col_kids = nullptr;
+    uint32_t* col_nint = nullptr;
+    int32_t* col_total = nullptr;
+    int64_t col_cap = 0;
     int64_t n_wide = 0;
     float* nbox = nullptr;         // [nt - 1][6] box of every binary node
     float* lbox = nullptr;         // [nt][6] padded box of every leaf
