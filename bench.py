@@ -4,7 +4,7 @@
 Workload (one step = one animated frame of the whole SDF update):
   coarse 256^3 / fine 512^3 fp32, 500 displaced UV spheres (1,000,000
   triangles), every object translated by a random vector of length <= 0.5
-  coarse voxel per frame; per frame: move objects, BVH rebuild, voxelize,
+  coarse voxel per frame; per frame: move objects, BVH rebuild (binned SAH), voxelize,
   jump flood (8 passes), mask + reset in changed regions, trace 64 Philox
   rays per masked fine texel with the Eq. 1 update.
 
@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--no-variant", action="store_true", help="skip the nearest-face sign variant comparison")
     ap.add_argument("--bvh", default="rebuild", choices=["rebuild", "refit"],
                     help="per-frame BVH maintenance: full rebuild (default) or refit of the first frame's tree")
+    ap.add_argument("--builder", default="sah", choices=["sah", "lbvh"],
+                    help="BVH topology: binned SAH (default) or Morton radix tree")
     ap.add_argument("--objects", type=int, default=N_OBJ, help="sphere count (500 = the 1M-triangle workload)")
     ap.add_argument("--coarse-n", type=int, default=NC, help="coarse grid size (256 = the benchmark workload; "
                                                               "smaller only for profiling captures)")
@@ -170,6 +172,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream(dev)
 
     rt = RTSDF(nc, beta_vox=BETA, seed=SEED)
+    rt.set_bvh_builder(args.builder)
     rt.upload_mesh(mesh.verts, mesh.tris)
     rt.set_objects(mesh.vert_object, mesh.n_objects)
     rt.build_bvh()
@@ -286,7 +289,7 @@ def run_gpu(args, rank, world):
         "data": "synthetic (seeded procedural scene: 500 displaced UV spheres, random rigid motion)",
         "config": {"workload": f"animated {nc}^3->{2 * nc}^3, {mesh.n_objects} spheres / {mesh.nt:,} tris, "
                                "64 rays/texel, d=2 voxels, beta=0.5, reset in changed regions, "
-                               f"per-frame BVH {args.bvh}+voxelize+JFA",
+                               f"per-frame BVH {args.bvh} ({args.builder})+voxelize+JFA",
                    "coarse_n": nc, "fine_n": 2 * nc, "triangles": int(mesh.nt), "rays_per_texel": RAYS,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (fine grids 3 x 512 MB)"},

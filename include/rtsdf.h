@@ -140,10 +140,33 @@ rtsdf_status rtsdf_set_objects(rtsdf_t ctx, const int32_t* vert_object, int32_t 
  * next rtsdf_sync and are clamped. */
 rtsdf_status rtsdf_move_objects(rtsdf_t ctx, const float* translations, int on_device);
 
-/* Builds (refit = 0) a linear BVH over the uploaded triangles (30-bit Morton
- * order, one triangle per leaf), or recomputes its boxes for the current
- * vertex positions keeping the topology (refit = 1; requires a build). */
+/* Builds (refit = 0) a binary BVH over the uploaded triangles, one triangle
+ * per leaf, collapsed to 4-wide nodes for the tracer, or recomputes its
+ * boxes for the current vertex positions keeping the topology (refit = 1;
+ * requires a build).  The topology comes from the context's builder
+ * (rtsdf_set_bvh_builder).  Traced results do not depend on the tree: every
+ * ray finds its closest hit (equal distances: smaller triangle index). */
 rtsdf_status rtsdf_build_bvh(rtsdf_t ctx, int refit);
+
+/* Topology of the next full build.
+ * RTSDF_BVH_SAH (default): top-down binned surface-area heuristic (32 bins
+ *   of the centroid bounds per axis; ranges of <= 32 triangles split at the
+ *   exact minimum over the centroids sorted along each axis).  About 13 %
+ *   fewer node visits per ray than the Morton tree, a slower build.
+ * RTSDF_BVH_LBVH: Karras' radix tree over 30-bit Morton codes of the
+ *   centroids (fastest build).
+ * RTSDF_E_ARG for an unknown builder. */
+typedef enum { RTSDF_BVH_LBVH = 0, RTSDF_BVH_SAH = 1 } rtsdf_bvh_builder;
+rtsdf_status rtsdf_set_bvh_builder(rtsdf_t ctx, int32_t builder);
+rtsdf_status rtsdf_get_bvh_builder(rtsdf_t ctx, int32_t* builder);
+
+/* Copies the binary topology of the last build to host memory (for checks
+ * and tools; synchronises the context's stream).  children: int32
+ * [nt - 1][2] (left, right) per node, a child >= 0 is a node, < 0 is
+ * ~(leaf position); leaf_tri: int32 [nt], the triangle of each leaf
+ * position; root: the root node (-1 when nt < 2).  Any pointer may be NULL
+ * to skip that output.  RTSDF_E_STATE without a build. */
+rtsdf_status rtsdf_get_bvh_topology(rtsdf_t ctx, int32_t* children, int32_t* leaf_tri, int32_t* root);
 
 /* Sec. 2.1: conservative voxelization.  A coarse voxel is a seed iff some
  * closed triangle meets the closed voxel cube (vertices quantised to 1/256

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librtsdf.so")
-SOURCES = ["api.cu", "voxelize.cu", "jfa.cu", "mask.cu", "bvh.cu", "trace.cu", "shadow.cu", "batch.cu", "tune.cu"]
+SOURCES = ["api.cu", "voxelize.cu", "jfa.cu", "mask.cu", "bvh.cu", "bvh_sah.cu", "trace.cu", "shadow.cu", "batch.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

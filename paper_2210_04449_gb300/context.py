@@ -116,6 +116,7 @@ class RTSDF:
         nv = int(np.prod(kv.shape)) // 3
         nt = int(np.prod(kt.shape)) // 3
         call("rtsdf_upload_mesh", self._h, pv, nv, pt, nt, dv)
+        self._nt = nt
 
     def set_objects(self, vert_object, n_objects: int) -> None:
         p, d, k = _host_or_device(vert_object, np.int32)
@@ -128,6 +129,29 @@ class RTSDF:
 
     def build_bvh(self, refit: bool = False) -> None:
         call("rtsdf_build_bvh", self._h, int(bool(refit)))
+
+    BVH_BUILDERS = {"lbvh": 0, "sah": 1}
+
+    def set_bvh_builder(self, builder: str) -> None:
+        """Topology of the next full build: "sah" (binned surface-area
+        heuristic, the default) or "lbvh" (Morton radix tree)."""
+        call("rtsdf_set_bvh_builder", self._h, self.BVH_BUILDERS[builder])
+
+    def get_bvh_builder(self) -> str:
+        v = ctypes.c_int32()
+        call("rtsdf_get_bvh_builder", self._h, ctypes.byref(v))
+        return {0: "lbvh", 1: "sah"}[v.value]
+
+    def bvh_topology(self):
+        """(children int32 [nt-1, 2], leaf_tri int32 [nt], root) of the last
+        build; a child < 0 is ~(leaf position)."""
+        nt = getattr(self, "_nt", 0)
+        ch = np.zeros((max(nt - 1, 0), 2), np.int32)
+        lt = np.zeros(nt, np.int32)
+        root = ctypes.c_int32()
+        call("rtsdf_get_bvh_topology", self._h, ch.ctypes.data if ch.size else None,
+             lt.ctypes.data if lt.size else None, ctypes.byref(root))
+        return ch, lt, root.value
 
     # ------------------------------------------------------------ Sec. 2.1-2.2
     def voxelize(self) -> None:

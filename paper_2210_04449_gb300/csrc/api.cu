@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -79,6 +80,8 @@ void free_all(rtsdf_ctx* c) {
     dfree(c->bvh.nodes); dfree(c->bvh.wide); dfree(c->bvh.nbox); dfree(c->bvh.lbox); dfree(c->bvh.tri); dfree(c->bvh.leaf_tri); dfree(c->bvh.leaf_parent); dfree(c->bvh.flags);
     dfree(c->bvh.col_fb); dfree(c->bvh.col_fslot); dfree(c->bvh.col_nb); dfree(c->bvh.col_nslot);
     dfree(c->bvh.col_kids); dfree(c->bvh.col_nint); dfree(c->bvh.col_total);
+    dfree(c->bvh.root); dfree(c->bvh.mk0); dfree(c->bvh.mk1); dfree(c->bvh.mv0); dfree(c->bvh.mv1);
+    dfree(c->bvh.hist); dfree(c->bvh.d_depth); dfree(c->bvh.sah);
     dfree(c->d_err);
     dfree(c->d_counters);
     for (auto& t : c->timers) {
@@ -594,6 +597,41 @@ rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
     if (!c || !mode) return RTSDF_E_ARG;
     *mode = c->sign_mode;
     return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_set_bvh_builder(rtsdf_t c, int32_t builder) {
+    if (!c || (builder != RTSDF_BVH_LBVH && builder != RTSDF_BVH_SAH)) return RTSDF_E_ARG;
+    c->bvh_builder = builder;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_get_bvh_builder(rtsdf_t c, int32_t* builder) {
+    if (!c || !builder) return RTSDF_E_ARG;
+    *builder = c->bvh_builder;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_get_bvh_topology(rtsdf_t c, int32_t* children, int32_t* leaf_tri, int32_t* root) {
+    if (!c) return RTSDF_E_ARG;
+    if (!c->bvh.built) return RTSDF_E_STATE;
+    DeviceGuard g(c->device);
+    const int64_t n = c->bvh.nt;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (!e && children && n > 1) {
+        std::vector<BNode> nodes((size_t)(n - 1));
+        e = cudaMemcpy(nodes.data(), c->bvh.nodes, sizeof(BNode) * (size_t)(n - 1), cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; !e && i < n - 1; i++) {
+            children[2 * i] = nodes[(size_t)i].d.x;
+            children[2 * i + 1] = nodes[(size_t)i].d.y;
+        }
+    }
+    if (!e && leaf_tri && n > 0)
+        e = cudaMemcpy(leaf_tri, c->bvh.leaf_tri, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost);
+    if (!e && root) {
+        *root = -1;
+        if (n > 1) e = cudaMemcpy(root, c->bvh.root, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    }
+    return from_cuda(e);
 }
 
 rtsdf_status rtsdf_sync(rtsdf_t c) {

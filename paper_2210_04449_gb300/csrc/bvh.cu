@@ -403,8 +403,8 @@ __global__ void k_collapse_write(const int32_t* __restrict__ fslot, int32_t cnt,
     if (i == cnt - 1) *total = (int32_t)(o + j);
 }
 
-__global__ void k_collapse_root(int32_t* fb, int32_t* fslot) {
-    fb[0] = 0;
+__global__ void k_collapse_root(const int32_t* root, int32_t* fb, int32_t* fslot) {
+    fb[0] = *root;
     fslot[0] = 0;
 }
 
@@ -437,7 +437,7 @@ static cudaError_t collapse_wide(rtsdf_ctx* c) {
         b.wide_cap = cap;
     }
     int32_t *fb = b.col_fb, *fs = b.col_fslot, *nb = b.col_nb, *ns = b.col_nslot;
-    RTSDF_LAUNCH(c, k_collapse_root, 1, 1, 0, fb, fs);
+    RTSDF_LAUNCH(c, k_collapse_root, 1, 1, 0, b.root, fb, fs);
     int32_t base = 1, cnt = 1;
     while (cnt > 0) {
         const unsigned g = (unsigned)((cnt + 255) / 256);
@@ -472,64 +472,77 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
         return cudaSuccess;
     }
     cudaError_t e;
-    // buffers (synchronous allocation: builds are not on the per-frame path)
-    auto realloc_if = [&](void** p, size_t bytes) -> cudaError_t {
-        if (*p) cudaFree(*p);
-        *p = nullptr;
-        return cudaMalloc(p, bytes > 0 ? bytes : 16);
-    };
+    const bool sah = c->bvh_builder == RTSDF_BVH_SAH && n > 1;
     const int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
-    if ((e = realloc_if((void**)&b.nodes, sizeof(BNode) * (size_t)(n > 1 ? n - 1 : 1)))) return e;
-    if ((e = realloc_if((void**)&b.tri, sizeof(float4) * TRI_F4 * (size_t)n))) return e;
-    if ((e = realloc_if((void**)&b.leaf_tri, sizeof(int32_t) * (size_t)n))) return e;
-    if ((e = realloc_if((void**)&b.leaf_parent, sizeof(int32_t) * (size_t)n))) return e;
-    if ((e = realloc_if((void**)&b.flags, sizeof(uint32_t) * (size_t)n))) return e;
-    if ((e = realloc_if((void**)&b.lbox, sizeof(float) * 6 * (size_t)n))) return e;
-    if ((e = realloc_if((void**)&b.nbox, sizeof(float) * 6 * (size_t)(n > 1 ? n - 1 : 1)))) return e;
-    uint32_t *k0 = nullptr, *k1 = nullptr, *hist = nullptr;
-    int32_t *v0 = nullptr, *v1 = nullptr, *depth = nullptr;
-    if ((e = cudaMalloc(&k0, sizeof(uint32_t) * n)) || (e = cudaMalloc(&k1, sizeof(uint32_t) * n)) ||
-        (e = cudaMalloc(&v0, sizeof(int32_t) * n)) || (e = cudaMalloc(&v1, sizeof(int32_t) * n)) ||
-        (e = cudaMalloc(&hist, sizeof(uint32_t) * 256 * (size_t)nblocks)) || (e = cudaMalloc(&depth, sizeof(int32_t)))) {
-        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(depth);
-        return e;
-    }
-    const float w = 2.f * c->cfg.extent;
-    const float lx = c->cfg.bmin[0] - 0.5f * c->cfg.extent, ly = c->cfg.bmin[1] - 0.5f * c->cfg.extent,
-                lz = c->cfg.bmin[2] - 0.5f * c->cfg.extent;
-    const unsigned g = (unsigned)((n + 255) / 256);
-    RTSDF_LAUNCH(c, k_morton, g, 256, 0, c->verts, c->tris, n, lx, ly, lz, 1.f / w, k0, v0);
-    uint32_t* kin = k0; uint32_t* kout = k1;
-    int32_t* vin = v0; int32_t* vout = v1;
-    for (int shift = 0; shift < 32; shift += 8) {
-        RTSDF_LAUNCH(c, k_hist, nblocks, SORT_THREADS, 0, kin, n, shift, hist, nblocks);
-        RTSDF_LAUNCH(c, k_scan, 1, 1024, 0, hist, (int64_t)256 * nblocks);
-        RTSDF_LAUNCH(c, k_scatter, nblocks, SORT_THREADS, 0, kin, vin, kout, vout, n, shift, hist, nblocks);
-        uint32_t* tk = kin; kin = kout; kout = tk;
-        int32_t* tv = vin; vin = vout; vout = tv;
-    }
-    // sorted keys in kin, triangle order in vin
-    if (n > 1) RTSDF_LAUNCH(c, k_karras, (unsigned)((n - 1 + 255) / 256), 256, 0, kin, vin, n, b.nodes, b.leaf_parent);
-    cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, c->stream);
-    const float pad = c->cfg.extent * 0x1p-16f;
-    RTSDF_LAUNCH(c, k_leaves_up, g, 256, 0, c->verts, c->tris, vin, n, b.tri, b.leaf_tri, b.leaf_parent, b.nodes,
-                 b.flags, pad, b.lbox, b.nbox);
-    cudaMemsetAsync(depth, 0, sizeof(int32_t), c->stream);
-    RTSDF_LAUNCH(c, k_depth, g, 256, 0, b.leaf_parent, b.nodes, n, depth);
-    if (n > 1) {
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = collapse_wide(c);
-        if (e != cudaSuccess) {
-            cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(depth);
+    // per-triangle arrays and scratch grow with the mesh and are kept across
+    // builds, so a per-frame rebuild allocates nothing
+    if (b.cap_nt < n) {
+        cudaFree(b.nodes); cudaFree(b.tri); cudaFree(b.leaf_tri); cudaFree(b.leaf_parent); cudaFree(b.flags);
+        cudaFree(b.lbox); cudaFree(b.nbox); cudaFree(b.mk0); cudaFree(b.mk1); cudaFree(b.mv0); cudaFree(b.mv1);
+        cudaFree(b.hist);
+        b.nodes = nullptr; b.tri = nullptr; b.leaf_tri = b.leaf_parent = nullptr; b.flags = nullptr;
+        b.lbox = b.nbox = nullptr; b.mk0 = b.mk1 = b.hist = nullptr; b.mv0 = b.mv1 = nullptr;
+        b.cap_nt = 0;
+        const size_t nn = (size_t)n;
+        if ((e = cudaMalloc(&b.nodes, sizeof(BNode) * (nn > 1 ? nn - 1 : 1))) ||
+            (e = cudaMalloc(&b.tri, sizeof(float4) * TRI_F4 * nn)) ||
+            (e = cudaMalloc(&b.leaf_tri, sizeof(int32_t) * nn)) ||
+            (e = cudaMalloc(&b.leaf_parent, sizeof(int32_t) * nn)) ||
+            (e = cudaMalloc(&b.flags, sizeof(uint32_t) * nn)) || (e = cudaMalloc(&b.lbox, sizeof(float) * 6 * nn)) ||
+            (e = cudaMalloc(&b.nbox, sizeof(float) * 6 * (nn > 1 ? nn - 1 : 1))) ||
+            (e = cudaMalloc(&b.mk0, sizeof(uint32_t) * nn)) || (e = cudaMalloc(&b.mk1, sizeof(uint32_t) * nn)) ||
+            (e = cudaMalloc(&b.mv0, sizeof(int32_t) * nn)) || (e = cudaMalloc(&b.mv1, sizeof(int32_t) * nn)) ||
+            (e = cudaMalloc(&b.hist, sizeof(uint32_t) * 256 * (size_t)nblocks)))
             return e;
-        }
+        b.cap_nt = n;
     }
-    e = cudaGetLastError();
+    if (!b.root && (e = cudaMalloc(&b.root, sizeof(int32_t)))) return e;
+    if (!b.d_depth && (e = cudaMalloc(&b.d_depth, sizeof(int32_t)))) return e;
+    if (sah && b.sah_bytes < sah_scratch_bytes(n)) {
+        cudaFree(b.sah);
+        b.sah = nullptr;
+        b.sah_bytes = 0;
+        if ((e = cudaMalloc(&b.sah, sah_scratch_bytes(n)))) return e;
+        b.sah_bytes = sah_scratch_bytes(n);
+    }
+    const unsigned g = (unsigned)((n + 255) / 256);
+    int32_t* order = b.mv0;                    // triangle at each leaf position
+    if (sah) {
+        if ((e = sah_topology(c, b.sah, order))) return e;
+    } else {
+        const float w = 2.f * c->cfg.extent;
+        const float lx = c->cfg.bmin[0] - 0.5f * c->cfg.extent, ly = c->cfg.bmin[1] - 0.5f * c->cfg.extent,
+                    lz = c->cfg.bmin[2] - 0.5f * c->cfg.extent;
+        RTSDF_LAUNCH(c, k_morton, g, 256, 0, c->verts, c->tris, n, lx, ly, lz, 1.f / w, b.mk0, b.mv0);
+        uint32_t* kin = b.mk0; uint32_t* kout = b.mk1;
+        int32_t* vin = b.mv0; int32_t* vout = b.mv1;
+        for (int shift = 0; shift < 32; shift += 8) {
+            RTSDF_LAUNCH(c, k_hist, nblocks, SORT_THREADS, 0, kin, n, shift, b.hist, nblocks);
+            RTSDF_LAUNCH(c, k_scan, 1, 1024, 0, b.hist, (int64_t)256 * nblocks);
+            RTSDF_LAUNCH(c, k_scatter, nblocks, SORT_THREADS, 0, kin, vin, kout, vout, n, shift, b.hist, nblocks);
+            uint32_t* tk = kin; kin = kout; kout = tk;
+            int32_t* tv = vin; vin = vout; vout = tv;
+        }
+        // four passes: sorted keys back in mk0, triangle order in mv0
+        order = vin;
+        if ((e = cudaMemsetAsync(b.root, 0, sizeof(int32_t), c->stream))) return e;
+        if (n > 1)
+            RTSDF_LAUNCH(c, k_karras, (unsigned)((n - 1 + 255) / 256), 256, 0, kin, vin, n, b.nodes, b.leaf_parent);
+    }
+    if ((e = cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, c->stream))) return e;
+    const float pad = c->cfg.extent * 0x1p-16f;
+    RTSDF_LAUNCH(c, k_leaves_up, g, 256, 0, c->verts, c->tris, order, n, b.tri, b.leaf_tri, b.leaf_parent, b.nodes,
+                 b.flags, pad, b.lbox, b.nbox);
+    if ((e = cudaMemsetAsync(b.d_depth, 0, sizeof(int32_t), c->stream))) return e;
+    RTSDF_LAUNCH(c, k_depth, g, 256, 0, b.leaf_parent, b.nodes, n, b.d_depth);
+    if (n > 1) {
+        if ((e = cudaGetLastError())) return e;
+        if ((e = collapse_wide(c))) return e;
+    }
+    if ((e = cudaGetLastError())) return e;
     int32_t hd = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hd, depth, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(depth);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&hd, b.d_depth, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream))) return e;
+    if ((e = cudaStreamSynchronize(c->stream))) return e;
     b.depth = hd;
     b.built = true;
     return cudaSuccess;

@@ -72,9 +72,22 @@ struct Bvh {
     int32_t* leaf_tri = nullptr;   // [nt] original triangle index of each leaf
     int32_t* leaf_parent = nullptr;// [nt]
     uint32_t* flags = nullptr;     // [nt] bottom-up visit counters
+    int32_t* root = nullptr;       // [1] binary root node (device)
+    int64_t cap_nt = 0;            // capacity of the per-triangle arrays above
+    // build scratch, kept across builds: Morton keys / order x 2, radix
+    // histograms, depth, and the SAH builder's arena
+    uint32_t *mk0 = nullptr, *mk1 = nullptr, *hist = nullptr;
+    int32_t *mv0 = nullptr, *mv1 = nullptr, *d_depth = nullptr;
+    void* sah = nullptr;
+    size_t sah_bytes = 0;
     int depth = 0;
     bool built = false;
 };
+
+// Binned-SAH topology (bvh_sah.cu): fills nodes[].d, leaf_parent, *root and
+// order[] (triangle at each leaf position) for nt >= 2.
+size_t sah_scratch_bytes(int64_t nt);
+cudaError_t sah_topology(rtsdf_ctx* c, void* scratch, int32_t* order);
 
 // Ring of event pairs per stage; summed (and emptied) by rtsdf_get_stats.
 constexpr int TIMER_RING = 128;
@@ -155,6 +168,7 @@ struct rtsdf_ctx {
 
     // launch parameters (rtsdf_set_tuning / rtsdf_autotune)
     int sign_mode = RTSDF_SIGN_VOTE;   // rtsdf_set_sign_mode
+    int bvh_builder = RTSDF_BVH_SAH;   // rtsdf_set_bvh_builder
     rtsdf_tuning tune = {4, 0, 12, 1024, 12};   // the autotuner's usual pick
 
     rtsdf::Bvh bvh;

@@ -49,6 +49,9 @@ def test_host_only_calls():
     assert lib.rtsdf_create(None, None) == 1
     assert lib.rtsdf_destroy(None) == 1
     assert lib.rtsdf_sync(None) == 1
+    assert lib.rtsdf_set_bvh_builder(None, 1) == 1
+    assert lib.rtsdf_get_bvh_builder(None, None) == 1
+    assert lib.rtsdf_get_bvh_topology(None, None, None, None) == 1
     cfg = _abi.Config()
     cfg.extent = 1.0
     cfg.coarse_n = 300          # above the 256 limit
