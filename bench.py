@@ -46,14 +46,11 @@ FLOP_PER_VISIT = 4 * (6 * 2 + 12 + 1) + 5
 FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
-# by the sha256 of the kernel sources it was measured on; reported as null
-# once trace.cu or trace_dev.cuh changes.
+# by the sha256 of the sources it was measured on (the kernel and the BVH
+# builders, whose tree it walks); reported as null once any of them changes.
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
-    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant" (1 pass):
-    # 12.08 GB + 177.08 MB
-    "e7380462910d1162": 12.08e9 + 177.08e6,
 }
+TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 
 
 def _src_hash(*names):
@@ -271,7 +268,7 @@ def run_gpu(args, rank, world):
     # node entries include the leaves; a leaf entry is one triangle test
     flop_per_ray = (visits_per_ray - tests_per_ray) * FLOP_PER_VISIT + tests_per_ray * FLOP_PER_TEST
     trace_tflops = rays_frame * flop_per_ray / (trace_ms * 1e-3) / 1e12 if trace_ms else None
-    th = _src_hash("trace.cu", "trace_dev.cuh")
+    th = _src_hash(*TRAFFIC_SOURCES)
     traffic = TRAFFIC.get(th)
 
     line = {
