@@ -49,6 +49,10 @@ FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 # by the sha256 of the sources it was measured on (the kernel and the BVH
 # builders, whose tree it walks); reported as null once any of them changes.
 TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
+    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant" (1 pass), SAH tree:
+    # 11.05 GB + 176.3 MB
+    "1135b1eb3fdbf31a": 11.0515e9 + 176.32e6,
 }
 TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 
@@ -289,7 +293,7 @@ def run_gpu(args, rank, world):
                                f"per-frame BVH {args.bvh} ({args.builder})+voxelize+JFA",
                    "coarse_n": nc, "fine_n": 2 * nc, "triangles": int(mesh.nt), "rays_per_texel": RAYS,
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (fine grids 3 x 512 MB)"},
+                   "l2": f"inputs larger than L2 (fine grids 3 x {(2 * nc) ** 3 * 4 >> 20} MB)"},
         "gpu_launches": int(launches),
         "rays_per_s": round(rays_frame / (trace_ms * 1e-3)) if trace_ms else None,
         "masked_texels": int(n_masked_tex),
@@ -534,11 +538,13 @@ def oracle_threads():
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    # budget ~2 minutes for the whole run
-    per_step_s = max(8.0, 150.0 / (args.steps + args.warmup))
+    # about 2.5 minutes for the whole run: per step ~1.6 s of voxelize + JFA +
+    # mask plus ~16 ms of brute-force tracing per sampled texel (16 Grace cores)
+    per_step_s = min(20.0, 150.0 / (args.steps + args.warmup))
+    n_tex = int(min(1024, max(8, (per_step_s - 1.6) / 0.016)))
     vals, info = [], None
     for i in range(args.warmup + args.steps):
-        ms, info = oracle_frame_sample(4 if per_step_s < 12 else 8)
+        ms, info = oracle_frame_sample(n_tex)
         if i >= args.warmup:
             vals.append(ms)
     v = sum(vals) / len(vals)
@@ -575,7 +581,8 @@ def main():
         line["sign_variant"] = run_sign_variant(torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            ms, info = oracle_frame_sample(16, masked_texels=m_tex)
+            # ~10 s of host work: the full coarse stages and 512 traced texels
+            ms, info = oracle_frame_sample(512, masked_texels=m_tex)
             line["cpu_baseline"] = {
                 "value": round(ms, 1), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                 "sample": f"one frame: voxelize + JFA + mask in full, brute-force trace of "
