@@ -94,8 +94,8 @@ def parse():
     ap.add_argument("--no-variant", action="store_true", help="skip the nearest-face sign variant comparison")
     ap.add_argument("--bvh", default="rebuild", choices=["rebuild", "refit"],
                     help="per-frame BVH maintenance: full rebuild (default) or refit of the first frame's tree")
-    ap.add_argument("--builder", default="sah", choices=["sah", "lbvh"],
-                    help="BVH topology: binned SAH (default) or Morton radix tree")
+    ap.add_argument("--builder", default="sah", choices=["sah", "lbvh", "two_level"],
+                    help="BVH topology: binned SAH (default), Morton radix tree, or two-level (per-object SAH subtrees under a top tree that a refit rebuilds)")
     ap.add_argument("--objects", type=int, default=N_OBJ, help="sphere count (500 = the 1M-triangle workload)")
     ap.add_argument("--coarse-n", type=int, default=NC, help="coarse grid size (256 = the benchmark workload; "
                                                               "smaller only for profiling captures)")

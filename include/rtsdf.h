@@ -155,8 +155,15 @@ rtsdf_status rtsdf_build_bvh(rtsdf_t ctx, int refit);
  *   fewer node visits per ray than the Morton tree, a slower build.
  * RTSDF_BVH_LBVH: Karras' radix tree over 30-bit Morton codes of the
  *   centroids (fastest build).
+ * RTSDF_BVH_TWO_LEVEL: for rigidly moving objects (rtsdf_set_objects): one
+ *   SAH subtree per object (triangles grouped by their first vertex's
+ *   object) under an SAH top tree over the objects.  A refit
+ *   (rtsdf_build_bvh(ctx, 1)) refits the subtrees in world space and
+ *   rebuilds the top tree, so the tree keeps its quality as objects move,
+ *   for a fraction of a full build.  Without objects, or with more than 1024
+ *   objects that own triangles, a build makes one SAH tree instead.
  * RTSDF_E_ARG for an unknown builder. */
-typedef enum { RTSDF_BVH_LBVH = 0, RTSDF_BVH_SAH = 1 } rtsdf_bvh_builder;
+typedef enum { RTSDF_BVH_LBVH = 0, RTSDF_BVH_SAH = 1, RTSDF_BVH_TWO_LEVEL = 2 } rtsdf_bvh_builder;
 rtsdf_status rtsdf_set_bvh_builder(rtsdf_t ctx, int32_t builder);
 rtsdf_status rtsdf_get_bvh_builder(rtsdf_t ctx, int32_t* builder);
 

@@ -130,17 +130,19 @@ class RTSDF:
     def build_bvh(self, refit: bool = False) -> None:
         call("rtsdf_build_bvh", self._h, int(bool(refit)))
 
-    BVH_BUILDERS = {"lbvh": 0, "sah": 1}
+    BVH_BUILDERS = {"lbvh": 0, "sah": 1, "two_level": 2}
 
     def set_bvh_builder(self, builder: str) -> None:
         """Topology of the next full build: "sah" (binned surface-area
-        heuristic, the default) or "lbvh" (Morton radix tree)."""
+        heuristic, the default), "lbvh" (Morton radix tree) or "two_level"
+        (an SAH subtree per object under a top tree that every refit
+        rebuilds)."""
         call("rtsdf_set_bvh_builder", self._h, self.BVH_BUILDERS[builder])
 
     def get_bvh_builder(self) -> str:
         v = ctypes.c_int32()
         call("rtsdf_get_bvh_builder", self._h, ctypes.byref(v))
-        return {0: "lbvh", 1: "sah"}[v.value]
+        return {0: "lbvh", 1: "sah", 2: "two_level"}[v.value]
 
     def bvh_topology(self):
         """(children int32 [nt-1, 2], leaf_tri int32 [nt], root) of the last

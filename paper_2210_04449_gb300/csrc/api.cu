@@ -82,6 +82,8 @@ void free_all(rtsdf_ctx* c) {
     dfree(c->bvh.col_kids); dfree(c->bvh.col_nint); dfree(c->bvh.col_total);
     dfree(c->bvh.root); dfree(c->bvh.mk0); dfree(c->bvh.mk1); dfree(c->bvh.mv0); dfree(c->bvh.mv1);
     dfree(c->bvh.hist); dfree(c->bvh.d_depth); dfree(c->bvh.sah);
+    dfree(c->bvh.top_child); dfree(c->bvh.top_ids); dfree(c->bvh.top_box); dfree(c->bvh.top_scratch);
+    dfree(c->bvh.obj_count);
     dfree(c->d_err);
     dfree(c->d_counters);
     for (auto& t : c->timers) {
@@ -320,6 +322,7 @@ rtsdf_status rtsdf_set_objects(rtsdf_t c, const int32_t* vert_object, int32_t n_
     cudaFree(tmp);
     if (s != RTSDF_OK) return s;
     c->n_obj = n_objects;
+    c->bvh.two_level = false;   // a two-level tree groups by the old objects: refits keep it whole
     return RTSDF_OK;
 }
 
@@ -600,7 +603,8 @@ rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
 }
 
 rtsdf_status rtsdf_set_bvh_builder(rtsdf_t c, int32_t builder) {
-    if (!c || (builder != RTSDF_BVH_LBVH && builder != RTSDF_BVH_SAH)) return RTSDF_E_ARG;
+    if (!c || (builder != RTSDF_BVH_LBVH && builder != RTSDF_BVH_SAH && builder != RTSDF_BVH_TWO_LEVEL))
+        return RTSDF_E_ARG;
     c->bvh_builder = builder;
     return RTSDF_OK;
 }

@@ -187,6 +187,36 @@ __device__ __forceinline__ void store_child(BNode* node, bool right, const float
     c[0] = lo[2]; c[1] = hi[2];
 }
 
+// Bottom-up boxes from `child` (a node id, or ~leaf) with box (lo, hi)
+// whose parent is `node`: each node takes the box of its first-arriving
+// child into its child slot and counts the arrival; the second arrival
+// forms the union and climbs on.  A negative parent ends the climb.
+__device__ __forceinline__ void climb(BNode* nodes, uint32_t* flags, float* __restrict__ nbox, int child, int node,
+                                      float lo[3], float hi[3], int64_t guard_n) {
+    // a tree over n leaves has depth < n; the guard only bounds the loop
+    for (int64_t guard = 0; node >= 0 && guard < guard_n; guard++) {
+        BNode* nd = nodes + node;
+        const bool right = nd->d.y == child;
+        store_child(nd, right, lo, hi);
+        __threadfence();
+        if (atomicAdd(flags + node, 1u) != 1u) return;   // first arrival: the sibling finishes this node
+        __threadfence();
+        // both children present: box of this node = union of its two child boxes
+        const volatile float* a = &nd->a.x;
+        const volatile float* b = &nd->b.x;
+        const volatile float* c = &nd->c.x;
+        lo[0] = fminf(a[0], b[0]); hi[0] = fmaxf(a[1], b[1]);
+        lo[1] = fminf(a[2], b[2]); hi[1] = fmaxf(a[3], b[3]);
+        lo[2] = fminf(c[0], c[2]); hi[2] = fmaxf(c[1], c[3]);
+        for (int k = 0; k < 3; k++) {
+            nbox[6 * (int64_t)node + k] = lo[k];
+            nbox[6 * (int64_t)node + 3 + k] = hi[k];
+        }
+        child = node;
+        node = nd->d.z;
+    }
+}
+
 // Leaf data + bottom-up boxes.  One thread per leaf.
 __global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __restrict__ tris,
                             const int32_t* order, int64_t n, float4* __restrict__ tri, int32_t* leaf_tri,
@@ -212,30 +242,54 @@ __global__ void k_leaves_up(const float* __restrict__ verts, const int32_t* __re
         lbox[6 * i + a] = lo[a];
         lbox[6 * i + 3 + a] = hi[a];
     }
-    int child = ~(int)i;
-    int node = leaf_parent[i];
-    // a tree over n leaves has depth < n; the guard only bounds the loop
-    for (int64_t guard = 0; node >= 0 && guard < n; guard++) {
-        BNode* nd = nodes + node;
-        const bool right = nd->d.y == child;
-        store_child(nd, right, lo, hi);
-        __threadfence();
-        if (atomicAdd(flags + node, 1u) != 1u) return;   // first arrival: the sibling finishes this node
-        __threadfence();
-        // both children present: box of this node = union of its two child boxes
-        const volatile float* a = &nd->a.x;
-        const volatile float* b = &nd->b.x;
-        const volatile float* c = &nd->c.x;
-        lo[0] = fminf(a[0], b[0]); hi[0] = fmaxf(a[1], b[1]);
-        lo[1] = fminf(a[2], b[2]); hi[1] = fmaxf(a[3], b[3]);
-        lo[2] = fminf(c[0], c[2]); hi[2] = fmaxf(c[1], c[3]);
-        for (int k = 0; k < 3; k++) {
-            nbox[6 * (int64_t)node + k] = lo[k];
-            nbox[6 * (int64_t)node + 3 + k] = hi[k];
-        }
-        child = node;
-        node = nd->d.z;
-    }
+    climb(nodes, flags, nbox, ~(int)i, leaf_parent[i], lo, hi, n);
+}
+
+// ------------------------------------------------------- two-level form
+
+// Object of each triangle (its first vertex's), and the identity order.
+__global__ void k_tri_object(const int32_t* __restrict__ tris, const int32_t* __restrict__ vobj, int64_t n,
+                             int n_obj, uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
+                             int32_t* __restrict__ count) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int o = min(max(vobj[tris[3 * t]], 0), n_obj - 1);
+    keys[t] = (uint32_t)o;
+    vals[t] = (int32_t)t;
+    atomicAdd(count + o, 1);
+}
+
+// Cut the listed subtrees off the top tree, so that a refit climb stops at
+// their roots.
+__global__ void k_top_detach(const int32_t* __restrict__ child, int32_t n, BNode* nodes, int32_t* leaf_parent) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int c = child[j];
+    if (c >= 0) nodes[c].d.z = -2;
+    else leaf_parent[~c] = -2;
+}
+
+// Box of each listed subtree (its root's box) for the top-tree build.
+__global__ void k_top_boxes(const int32_t* __restrict__ child, int32_t n, const float* __restrict__ nbox,
+                            const float* __restrict__ lbox, float4* __restrict__ box) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int c = child[j];
+    const float* p = c >= 0 ? nbox + 6 * (int64_t)c : lbox + 6 * (int64_t)(~c);
+    box[2 * j] = make_float4(p[0], p[1], p[2], 0.f);
+    box[2 * j + 1] = make_float4(p[3], p[4], p[5], 0.f);
+}
+
+// Boxes of the top tree: climb from every listed subtree root.
+__global__ void k_top_up(const int32_t* __restrict__ child, int32_t n, const int32_t* __restrict__ leaf_parent,
+                         BNode* nodes, uint32_t* flags, const float* __restrict__ lbox, float* __restrict__ nbox,
+                         int64_t nt) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int c = child[j];
+    const float* p = c >= 0 ? nbox + 6 * (int64_t)c : lbox + 6 * (int64_t)(~c);
+    float lo[3] = {p[0], p[1], p[2]}, hi[3] = {p[3], p[4], p[5]};
+    climb(nodes, flags, nbox, c, c >= 0 ? nodes[c].d.z : leaf_parent[~c], lo, hi, nt);
 }
 
 // Child boxes of the 4-wide nodes from the (re)fitted binary boxes.
@@ -460,6 +514,94 @@ static cudaError_t collapse_wide(rtsdf_ctx* c) {
     return cudaGetLastError();
 }
 
+// Two-level topology: triangles sorted by object (stable), one SAH subtree
+// per object, and the top tree over the objects' subtrees.  Sets *order to
+// the leaf order.  *applies = false (nothing built) when the form does not
+// apply: no objects, or more than SAH_TOP_MAX objects with triangles.
+static cudaError_t two_level_topology(rtsdf_ctx* c, int32_t** order, bool* applies) {
+    Bvh& b = c->bvh;
+    const int64_t n = b.nt;
+    const int n_obj = c->n_obj;
+    *applies = false;
+    b.two_level = false;
+    if (n < 2 || n_obj < 1 || !c->vert_obj) return cudaSuccess;
+    cudaError_t e;
+    if (b.obj_cap < n_obj) {
+        cudaFree(b.obj_count);
+        b.obj_count = nullptr;
+        b.obj_cap = 0;
+        if ((e = cudaMalloc(&b.obj_count, sizeof(int32_t) * (size_t)n_obj))) return e;
+        b.obj_cap = n_obj;
+    }
+    const unsigned g = (unsigned)((n + 255) / 256);
+    const int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    if ((e = cudaMemsetAsync(b.obj_count, 0, sizeof(int32_t) * (size_t)n_obj, c->stream))) return e;
+    RTSDF_LAUNCH(c, k_tri_object, g, 256, 0, c->tris, c->vert_obj, n, n_obj, b.mk0, b.mv0, b.obj_count);
+    int bits = 1;
+    while (bits < 32 && (1u << bits) < (unsigned)n_obj) bits++;
+    uint32_t* kin = b.mk0; uint32_t* kout = b.mk1;
+    int32_t* vin = b.mv0; int32_t* vout = b.mv1;
+    for (int shift = 0; shift < bits; shift += 8) {
+        RTSDF_LAUNCH(c, k_hist, nblocks, SORT_THREADS, 0, kin, n, shift, b.hist, nblocks);
+        RTSDF_LAUNCH(c, k_scan, 1, 1024, 0, b.hist, (int64_t)256 * nblocks);
+        RTSDF_LAUNCH(c, k_scatter, nblocks, SORT_THREADS, 0, kin, vin, kout, vout, n, shift, b.hist, nblocks);
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        int32_t* tv = vin; vin = vout; vout = tv;
+    }
+    std::vector<int32_t> count((size_t)n_obj);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = cudaMemcpyAsync(count.data(), b.obj_count, sizeof(int32_t) * (size_t)n_obj, cudaMemcpyDeviceToHost,
+                             c->stream)))
+        return e;
+    if ((e = cudaStreamSynchronize(c->stream))) return e;
+    std::vector<int32_t> bounds(1, 0);
+    for (int o = 0; o < n_obj; o++)
+        if (count[(size_t)o] > 0) bounds.push_back(bounds.back() + count[(size_t)o]);
+    const int32_t k = (int32_t)bounds.size() - 1;
+    if (k < 1 || k > SAH_TOP_MAX || bounds.back() != n) return cudaSuccess;
+    if (b.top_cap < k) {
+        cudaFree(b.top_child); cudaFree(b.top_ids); cudaFree(b.top_box); cudaFree(b.top_scratch);
+        b.top_child = b.top_ids = nullptr;
+        b.top_box = nullptr;
+        b.top_scratch = nullptr;
+        b.top_cap = 0;
+        if ((e = cudaMalloc(&b.top_child, sizeof(int32_t) * (size_t)k)) ||
+            (e = cudaMalloc(&b.top_ids, sizeof(int32_t) * (size_t)k)) ||
+            (e = cudaMalloc(&b.top_box, sizeof(float4) * 2 * (size_t)k)) ||
+            (e = cudaMalloc(&b.top_scratch, sah_top_bytes(SAH_TOP_MAX))))
+            return e;
+        b.top_cap = k;
+    }
+    // leaves of one-triangle objects keep parent -1 until the top tree takes them
+    if ((e = cudaMemsetAsync(b.leaf_parent, 0xFF, sizeof(int32_t) * (size_t)n, c->stream))) return e;
+    int32_t* out = vin == b.mv0 ? b.mv1 : b.mv0;
+    if ((e = sah_segments(c, b.sah, out, vin, bounds.data(), k, b.top_child))) return e;
+    // the top tree's nodes own the boundaries between objects
+    std::vector<int32_t> ids((size_t)k, 0);
+    for (int32_t j = 0; j + 1 < k; j++) ids[(size_t)j] = bounds[(size_t)j + 1] - 1;
+    if ((e = cudaMemcpyAsync(b.top_ids, ids.data(), sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, c->stream)))
+        return e;
+    if ((e = sah_top_prepare(c, b.top_scratch, k))) return e;   // synchronises: ids may go
+    b.top_n = k;
+    b.two_level = true;
+    *applies = true;
+    *order = out;
+    return cudaSuccess;
+}
+
+// Top tree of the two-level form over its subtrees, whose boxes are fitted
+// (flags of the top nodes zero), then the top boxes.
+static cudaError_t build_top(rtsdf_ctx* c) {
+    Bvh& b = c->bvh;
+    const unsigned gk = (unsigned)((b.top_n + 127) / 128);
+    RTSDF_LAUNCH(c, k_top_boxes, gk, 128, 0, b.top_child, b.top_n, b.nbox, b.lbox, b.top_box);
+    cudaError_t e = sah_top(c, b.top_scratch, b.top_n, b.top_box, b.top_ids, b.top_child);
+    if (e) return e;
+    RTSDF_LAUNCH(c, k_top_up, gk, 128, 0, b.top_child, b.top_n, b.leaf_parent, b.nodes, b.flags, b.lbox, b.nbox,
+                 b.nt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     Bvh& b = c->bvh;
     const int64_t n = c->nt;
@@ -472,7 +614,8 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
         return cudaSuccess;
     }
     cudaError_t e;
-    const bool sah = c->bvh_builder == RTSDF_BVH_SAH && n > 1;
+    // the two-level form falls back to one SAH tree where it does not apply
+    const bool sah = c->bvh_builder != RTSDF_BVH_LBVH && n > 1;
     const int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
     // per-triangle arrays and scratch grow with the mesh and are kept across
     // builds, so a per-frame rebuild allocates nothing
@@ -507,7 +650,11 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     }
     const unsigned g = (unsigned)((n + 255) / 256);
     int32_t* order = b.mv0;                    // triangle at each leaf position
-    if (sah) {
+    bool two = false;
+    if (c->bvh_builder == RTSDF_BVH_TWO_LEVEL && (e = two_level_topology(c, &order, &two))) return e;
+    if (two) {
+        // topology below the top tree done; the top tree follows the boxes
+    } else if (sah) {
         if ((e = sah_topology(c, b.sah, order))) return e;
     } else {
         const float w = 2.f * c->cfg.extent;
@@ -533,6 +680,7 @@ cudaError_t launch_bvh_build(rtsdf_ctx* c) {
     const float pad = c->cfg.extent * 0x1p-16f;
     RTSDF_LAUNCH(c, k_leaves_up, g, 256, 0, c->verts, c->tris, order, n, b.tri, b.leaf_tri, b.leaf_parent, b.nodes,
                  b.flags, pad, b.lbox, b.nbox);
+    if (two && (e = build_top(c))) return e;
     if ((e = cudaMemsetAsync(b.d_depth, 0, sizeof(int32_t), c->stream))) return e;
     RTSDF_LAUNCH(c, k_depth, g, 256, 0, b.leaf_parent, b.nodes, n, b.d_depth);
     if (n > 1) {
@@ -555,6 +703,15 @@ cudaError_t launch_bvh_refit(rtsdf_ctx* c) {
     cudaError_t e = cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, c->stream);
     if (e != cudaSuccess) return e;
     const float pad = c->cfg.extent * 0x1p-16f;
+    if (b.two_level) {
+        // refit the objects' subtrees, then rebuild the top tree over them
+        RTSDF_LAUNCH(c, k_top_detach, (unsigned)((b.top_n + 127) / 128), 128, 0, b.top_child, b.top_n, b.nodes,
+                     b.leaf_parent);
+        RTSDF_LAUNCH(c, k_leaves_up, (unsigned)((n + 255) / 256), 256, 0, c->verts, c->tris, b.leaf_tri, n, b.tri,
+                     b.leaf_tri, b.leaf_parent, b.nodes, b.flags, pad, b.lbox, b.nbox);
+        if ((e = build_top(c))) return e;
+        return collapse_wide(c);
+    }
     RTSDF_LAUNCH(c, k_leaves_up, (unsigned)((n + 255) / 256), 256, 0, c->verts, c->tris, b.leaf_tri, n, b.tri,
                  b.leaf_tri, b.leaf_parent, b.nodes, b.flags, pad, b.lbox, b.nbox);
     if (b.n_wide > 0)

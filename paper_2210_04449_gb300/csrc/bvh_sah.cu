@@ -25,6 +25,10 @@
 // every merge is exact and independent of order: the build is
 // deterministic, whatever order the atomics land in.
 #include <math_constants.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -170,11 +174,48 @@ __device__ Choice warp_choose(const uint32_t* bins, int lane) {
     return best;
 }
 
-// Hook `child` (a node id or ~leaf position) under `parent` on `side`.
-__device__ __forceinline__ void link(BNode* nodes, int32_t* root, int parent, int side, int child) {
-    if (parent < 0) *root = child;
-    else if (side) nodes[parent].d.y = child;
-    else nodes[parent].d.x = child;
+// Where a build writes its topology.  A parent id >= 0 is a node, -1 the
+// tree's root, <= -2 the root of segment -2 - parent (per-segment builds).
+// A top-level build over segments (child_of set) names its nodes through
+// node_ids (local id -> node) and makes each of its leaves the subtree
+// child_of[item] of the listed segment `item`.
+struct Links {
+    BNode* nodes;
+    int32_t* leaf_parent;
+    int32_t* root;
+    int32_t* seg_root;
+    const int32_t* node_ids;
+    const int32_t* child_of;
+};
+
+__device__ __forceinline__ void hook(const Links& L, int parent, int side, int child) {
+    if (parent >= 0) {
+        if (side) L.nodes[parent].d.y = child;
+        else L.nodes[parent].d.x = child;
+    } else if (parent == -1) {
+        *L.root = child;
+    } else {
+        L.seg_root[-2 - parent] = child;
+    }
+}
+
+__device__ __forceinline__ void make_node(const Links& L, int id, int parent, int side) {
+    L.nodes[id].d.z = parent;
+    L.nodes[id].d.w = 0;
+    hook(L, parent, side, id);
+}
+
+// Leaf at global position pos, or in a top-level build the subtree of item.
+__device__ __forceinline__ void make_leaf(const Links& L, int parent, int side, int pos, int item) {
+    if (L.child_of) {
+        const int c = L.child_of[item];
+        hook(L, parent, side, c);
+        if (c >= 0) L.nodes[c].d.z = parent;
+        else L.leaf_parent[~c] = parent;
+    } else {
+        hook(L, parent, side, ~pos);
+        L.leaf_parent[pos] = parent;
+    }
 }
 
 // Exclusive block-wide sum (all SAH_THREADS threads call).
@@ -224,8 +265,9 @@ __global__ void k_sah_root(SahTask* t, int4* chunks, uint32_t* bins, SahRange* b
     }
 }
 
-// Per triangle: its box (unpadded), the identity order, the root's
-// centroid bounds.
+// Per triangle: its box (unpadded); for a single-root build also the
+// identity order and the root's centroid bounds (ord, root: nullptr for a
+// segment build).
 __global__ void __launch_bounds__(SAH_THREADS) k_sah_prims(const float* __restrict__ verts,
                                                            const int32_t* __restrict__ tris, int32_t n,
                                                            float4* __restrict__ pbox, int32_t* __restrict__ ord,
@@ -248,8 +290,9 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_prims(const float* __restri
         }
         pbox[2 * (int64_t)i] = make_float4(lo[0], lo[1], lo[2], 0.f);
         pbox[2 * (int64_t)i + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
-        ord[i] = i;
+        if (ord) ord[i] = i;
     }
+    if (!root) return;                          // block-uniform: segment builds set their own bounds
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
@@ -270,6 +313,52 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_prims(const float* __restri
             else atomicMax(&root->cb[k], f2o(v));
         }
     }
+}
+
+// Centroid bounds of the first level's big ranges of a segment build (one
+// block per range) and their bins reset.
+__global__ void __launch_bounds__(SAH_THREADS) k_sah_task_init(SahTask* tasks, const int32_t* __restrict__ ord,
+                                                               const float4* __restrict__ pbox, uint32_t* bins) {
+    __shared__ float s_red[SAH_WARPS][6];
+    SahTask& T = tasks[blockIdx.x];
+    float r[6] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F};
+    for (int p = T.b + threadIdx.x; p < T.e; p += SAH_THREADS) {
+        const int32_t t = ord[p];
+        const float4 lo = pbox[2 * (int64_t)t], hi = pbox[2 * (int64_t)t + 1];
+        const float c[3] = {cen(lo.x, hi.x), cen(lo.y, hi.y), cen(lo.z, hi.z)};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            r[k] = fminf(r[k], c[k]);
+            r[3 + k] = fmaxf(r[3 + k], c[k]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            r[k] = fminf(r[k], __shfl_xor_sync(FULL, r[k], o));
+            r[3 + k] = fmaxf(r[3 + k], __shfl_xor_sync(FULL, r[3 + k], o));
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 6; k++) s_red[warp][k] = r[k];
+    for (int i = threadIdx.x; i < SAH_BIN_WORDS; i += SAH_THREADS)
+        bins[(size_t)blockIdx.x * SAH_BIN_WORDS + i] = bin_init(i);
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        float v = s_red[0][k];
+        for (int w = 1; w < SAH_WARPS; w++) v = k < 3 ? fminf(v, s_red[w][k]) : fmaxf(v, s_red[w][k]);
+        T.cb[k] = f2o(v);                       // a big range is never empty
+    }
+}
+
+// A top-level tree over a single segment: the segment's subtree is the root.
+__global__ void k_sah_top_single(const int32_t* child_of, BNode* nodes, int32_t* leaf_parent, int32_t* root) {
+    const int c = child_of[0];
+    *root = c;
+    if (c >= 0) nodes[c].d.z = -1;
+    else leaf_parent[~c] = -1;
 }
 
 // ------------------------------------------------------------- big ranges
@@ -327,8 +416,7 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_bin(const int4* __restrict_
 __global__ void __launch_bounds__(SAH_THREADS) k_sah_split(SahTask* tasks, int32_t ntask, const uint32_t* bins,
                                                            const uint32_t* __restrict__ hist,
                                                            const int4* __restrict__ chunks,
-                                                           int32_t* __restrict__ left_off, BNode* nodes,
-                                                           int32_t* leaf_parent, int32_t* root, SahTask* next,
+                                                           int32_t* __restrict__ left_off, Links L, SahTask* next,
                                                            int4* next_chunks, uint32_t* next_bins, SahRange* blist,
                                                            int32_t* counters, int32_t cap_task, int32_t cap_chunk,
                                                            int32_t cap_blist) {
@@ -367,10 +455,7 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_split(SahTask* tasks, int32
     for (int s = 0; s < 2; s++) {
         const int cb = s ? b + nl : b, ce = s ? e : b + nl, cm = ce - cb;
         if (cm == 1) {
-            if (lane == 0) {
-                link(nodes, root, id, s, ~cb);
-                leaf_parent[cb] = id;
-            }
+            if (lane == 0) make_leaf(L, id, s, cb, -1);
         } else if (cm <= SAH_CH) {
             if (lane == 0) {
                 const int q = atomicAdd(counters + 2, 1);
@@ -409,9 +494,7 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_split(SahTask* tasks, int32
         }
     }
     if (lane == 0) {
-        nodes[id].d.z = T.parent;
-        nodes[id].d.w = 0;
-        link(nodes, root, T.parent, T.side, id);
+        make_node(L, id, T.parent, T.side);
         T.axis = ch.axis;
         T.split = ch.split;
         T.nl = nl;
@@ -515,8 +598,7 @@ struct BlockSmem {
 // Exact heuristic for a range of <= 32 positions, one warp; sub-ranges on a
 // warp-private stack.  Positions are local to the block's range (global
 // position = gb + local).
-__device__ void warp_exact(BlockSmem& S, SahRange r0, int gb, BNode* nodes, int32_t* leaf_parent, int32_t* root,
-                           int lane, SahRange* st) {
+__device__ void warp_exact(BlockSmem& S, SahRange r0, int gb, const Links& L, int lane, SahRange* st) {
     int top = 1;
     if (lane == 0) st[0] = r0;
     __syncwarp();
@@ -608,19 +690,12 @@ __device__ void warp_exact(BlockSmem& S, SahRange r0, int gb, BNode* nodes, int3
             if (lane < mm) S.perm[lb + lane] = (uint16_t)ns;
             __syncwarp();
         }
-        const int id = gb + lb + nl - 1;
-        if (lane == 0) {
-            nodes[id].d.z = r.parent;
-            nodes[id].d.w = 0;
-            link(nodes, root, r.parent, r.sb & 1, id);
-        }
+        const int id = L.node_ids ? L.node_ids[lb + nl - 1] : gb + lb + nl - 1;
+        if (lane == 0) make_node(L, id, r.parent, r.sb & 1);
         for (int s = 0; s < 2; s++) {
             const int cb = s ? lb + nl : lb, ce = s ? r.e : lb + nl;
             if (ce - cb == 1) {
-                if (lane == 0) {
-                    link(nodes, root, id, s, ~(gb + cb));
-                    leaf_parent[gb + cb] = id;
-                }
+                if (lane == 0) make_leaf(L, id, s, gb + cb, S.tri[S.perm[cb]]);
             } else {
                 if (lane == 0 && top < WSTACK) st[top] = SahRange{cb, ce, id, s};
                 top++;
@@ -638,8 +713,8 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_block(const SahRange* __res
                                                            const int32_t* __restrict__ ord0,
                                                            const int32_t* __restrict__ ord1,
                                                            const float4* __restrict__ pbox,
-                                                           int32_t* __restrict__ order_final, BNode* nodes,
-                                                           int32_t* leaf_parent, int32_t* root, int32_t* counters) {
+                                                           int32_t* __restrict__ order_final, Links L,
+                                                           int32_t* counters) {
     extern __shared__ __align__(16) unsigned char sah_smem[];
     BlockSmem& S = *reinterpret_cast<BlockSmem*>(sah_smem);
     const SahRange R = blist[blockIdx.x];
@@ -750,16 +825,13 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_block(const SahRange* __res
         __syncthreads();
         for (int p = lb + tid; p < le; p += SAH_THREADS) S.perm[p] = S.tmp[p];
         if (tid == 0) {
-            const int id = gb + lb + nl - 1;
-            nodes[id].d.z = r.parent;
-            nodes[id].d.w = 0;
-            link(nodes, root, r.parent, r.sb & 1, id);
+            const int id = L.node_ids ? L.node_ids[lb + nl - 1] : gb + lb + nl - 1;
+            make_node(L, id, r.parent, r.sb & 1);
             for (int s = 0; s < 2; s++) {
                 const int cb0 = s ? lb + nl : lb, ce = s ? le : lb + nl, cm = ce - cb0;
                 const SahRange ch{cb0, ce, id, s};
                 if (cm == 1) {
-                    link(nodes, root, id, s, ~(gb + cb0));
-                    leaf_parent[gb + cb0] = id;
+                    make_leaf(L, id, s, gb + cb0, S.tri[S.tmp[cb0]]);   // tmp: this range's new order
                 } else if (cm <= WARP_MAX) {
                     if (S.nw < WLIST_CAP) S.wlist[S.nw++] = ch;
                     else S.bad = 1;
@@ -771,9 +843,10 @@ __global__ void __launch_bounds__(SAH_THREADS) k_sah_block(const SahRange* __res
         }
         __syncthreads();
     }
-    for (int q = warp; q < S.nw; q += SAH_WARPS) warp_exact(S, S.wlist[q], gb, nodes, leaf_parent, root, lane, S.wstack[warp]);
+    for (int q = warp; q < S.nw; q += SAH_WARPS) warp_exact(S, S.wlist[q], gb, L, lane, S.wstack[warp]);
     __syncthreads();
-    for (int i = tid; i < m; i += SAH_THREADS) order_final[gb + i] = S.tri[S.perm[i]];
+    if (order_final)
+        for (int i = tid; i < m; i += SAH_THREADS) order_final[gb + i] = S.tri[S.perm[i]];
     if (tid == 0 && (S.bad || S.top != 0)) atomicOr(counters + 3, 2);
 }
 
@@ -789,35 +862,43 @@ size_t sah_scratch_bytes(int64_t n) {
            16 * 256;   // alignment slack
 }
 
-// Topology of the binary tree over nt >= 2 triangles into b.nodes[].d,
-// b.leaf_parent, *b.root and order[] (triangle at each leaf position).
-// scratch: sah_scratch_bytes(nt) bytes of device memory.
-cudaError_t sah_topology(rtsdf_ctx* c, void* scratch, int32_t* order) {
-    Bvh& bv = c->bvh;
-    const int32_t n = (int32_t)bv.nt;
-    const int32_t cap_task = n / (SAH_CH + 1) + 2;
-    const int32_t cap_chunk = 2 * (n / SAH_CH) + 4;
-    const int32_t cap_blist = n / 2 + 2;
+namespace {
+
+struct SahArena {
+    float4* pbox;
+    int32_t *ord0, *ord1, *loff, *counters;
+    uint32_t* hist;
+    SahTask* tasks[2];
+    int4* chunks[2];
+    uint32_t* bins[2];
+    SahRange* blist;
+    int32_t cap_task, cap_chunk, cap_blist;
+};
+
+cudaError_t carve(void* scratch, int32_t n, SahArena& A) {
+    A.cap_task = n / (SAH_CH + 1) + 2;
+    A.cap_chunk = 2 * (n / SAH_CH) + 4;
+    A.cap_blist = n / 2 + 2;
     unsigned char* p = (unsigned char*)scratch;
     auto take = [&](size_t bytes) {
         void* r = p;
         p += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    float4* pbox = (float4*)take(sizeof(float4) * 2 * (size_t)n);
-    int32_t* ord0 = (int32_t*)take(sizeof(int32_t) * (size_t)n);
-    int32_t* ord1 = (int32_t*)take(sizeof(int32_t) * (size_t)n);
-    uint32_t* hist = (uint32_t*)take(sizeof(uint32_t) * 3 * NB * (size_t)cap_chunk);
-    int32_t* loff = (int32_t*)take(sizeof(int32_t) * (size_t)cap_chunk);
-    SahTask* tasks[2] = {(SahTask*)take(sizeof(SahTask) * (size_t)cap_task),
-                         (SahTask*)take(sizeof(SahTask) * (size_t)cap_task)};
-    int4* chunks[2] = {(int4*)take(sizeof(int4) * (size_t)cap_chunk), (int4*)take(sizeof(int4) * (size_t)cap_chunk)};
-    uint32_t* bins[2] = {(uint32_t*)take(sizeof(uint32_t) * SAH_BIN_WORDS * (size_t)cap_task),
-                         (uint32_t*)take(sizeof(uint32_t) * SAH_BIN_WORDS * (size_t)cap_task)};
-    SahRange* blist = (SahRange*)take(sizeof(SahRange) * (size_t)cap_blist);
-    int32_t* counters = (int32_t*)take(16 * sizeof(int32_t));
-    if ((size_t)(p - (unsigned char*)scratch) > sah_scratch_bytes(n)) return cudaErrorInvalidValue;
+    A.pbox = (float4*)take(sizeof(float4) * 2 * (size_t)n);
+    A.ord0 = (int32_t*)take(sizeof(int32_t) * (size_t)n);
+    A.ord1 = (int32_t*)take(sizeof(int32_t) * (size_t)n);
+    A.hist = (uint32_t*)take(sizeof(uint32_t) * 3 * NB * (size_t)A.cap_chunk);
+    A.loff = (int32_t*)take(sizeof(int32_t) * (size_t)A.cap_chunk);
+    for (int k = 0; k < 2; k++) A.tasks[k] = (SahTask*)take(sizeof(SahTask) * (size_t)A.cap_task);
+    for (int k = 0; k < 2; k++) A.chunks[k] = (int4*)take(sizeof(int4) * (size_t)A.cap_chunk);
+    for (int k = 0; k < 2; k++) A.bins[k] = (uint32_t*)take(sizeof(uint32_t) * SAH_BIN_WORDS * (size_t)A.cap_task);
+    A.blist = (SahRange*)take(sizeof(SahRange) * (size_t)A.cap_blist);
+    A.counters = (int32_t*)take(16 * sizeof(int32_t));
+    return (size_t)(p - (unsigned char*)scratch) > sah_scratch_bytes(n) ? cudaErrorInvalidValue : cudaSuccess;
+}
 
+cudaError_t block_attr(rtsdf_ctx* c) {
     static bool attr_set[64] = {};             // per device ordinal
     const int dv = c->device >= 0 && c->device < 64 ? c->device : 0;
     if (!attr_set[dv]) {
@@ -826,43 +907,163 @@ cudaError_t sah_topology(rtsdf_ctx* c, void* scratch, int32_t* order) {
         if (e != cudaSuccess) return e;
         attr_set[dv] = true;
     }
-    cudaError_t e = cudaMemsetAsync(counters, 0, 16 * sizeof(int32_t), c->stream);
-    if (e != cudaSuccess) return e;
-    const int nch0 = (n + SAH_CH - 1) / SAH_CH;
-    const int init_threads = nch0 > SAH_BIN_WORDS ? nch0 : SAH_BIN_WORDS;
-    RTSDF_LAUNCH(c, k_sah_root, (unsigned)((init_threads + 255) / 256), 256, 0, tasks[0], chunks[0], bins[0], blist, n);
-    RTSDF_LAUNCH(c, k_sah_prims, (unsigned)((n + SAH_THREADS - 1) / SAH_THREADS), SAH_THREADS, 0, c->verts, c->tris,
-                 n, pbox, ord0, tasks[0]);
-    int32_t ntask = n > SAH_CH ? 1 : 0, nchunk = nch0, nblock = n > SAH_CH ? 0 : 1;
+    return cudaSuccess;
+}
+
+// The level loop over big ranges, then the block ranges; ntask / nchunk /
+// nblock describe the first level (already in A).
+cudaError_t run_levels(rtsdf_ctx* c, SahArena& A, const Links& L, int32_t* order, int32_t ntask, int32_t nchunk,
+                       int32_t nblock) {
+    cudaError_t e;
     int cur = 0;
     for (int level = 0; ntask > 0; level++) {
         if (level >= 4096) return cudaErrorUnknown;   // sizes shrink every level; only a fault gets here
-        if ((e = cudaMemsetAsync(counters, 0, 2 * sizeof(int32_t), c->stream))) return e;
-        RTSDF_LAUNCH(c, k_sah_bin, (unsigned)nchunk, SAH_THREADS, 0, chunks[cur], tasks[cur], ord0, ord1, pbox,
-                     bins[cur], hist);
-        RTSDF_LAUNCH(c, k_sah_split, (unsigned)((ntask + SAH_WARPS - 1) / SAH_WARPS), SAH_THREADS, 0, tasks[cur],
-                     ntask, bins[cur], hist, chunks[cur], loff, bv.nodes, bv.leaf_parent, bv.root, tasks[cur ^ 1],
-                     chunks[cur ^ 1], bins[cur ^ 1], blist, counters, cap_task, cap_chunk, cap_blist);
-        RTSDF_LAUNCH(c, k_sah_partition, (unsigned)nchunk, SAH_THREADS, 0, chunks[cur], tasks[cur], loff, ord0, ord1,
-                     pbox, order, tasks[cur ^ 1]);
+        if ((e = cudaMemsetAsync(A.counters, 0, 2 * sizeof(int32_t), c->stream))) return e;
+        RTSDF_LAUNCH(c, k_sah_bin, (unsigned)nchunk, SAH_THREADS, 0, A.chunks[cur], A.tasks[cur], A.ord0, A.ord1,
+                     A.pbox, A.bins[cur], A.hist);
+        RTSDF_LAUNCH(c, k_sah_split, (unsigned)((ntask + SAH_WARPS - 1) / SAH_WARPS), SAH_THREADS, 0, A.tasks[cur],
+                     ntask, A.bins[cur], A.hist, A.chunks[cur], A.loff, L, A.tasks[cur ^ 1], A.chunks[cur ^ 1],
+                     A.bins[cur ^ 1], A.blist, A.counters, A.cap_task, A.cap_chunk, A.cap_blist);
+        RTSDF_LAUNCH(c, k_sah_partition, (unsigned)nchunk, SAH_THREADS, 0, A.chunks[cur], A.tasks[cur], A.loff, A.ord0,
+                     A.ord1, A.pbox, order, A.tasks[cur ^ 1]);
         int32_t h[4] = {0, 0, 0, 0};
         if ((e = cudaGetLastError())) return e;
-        if ((e = cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream))) return e;
+        if ((e = cudaMemcpyAsync(h, A.counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream))) return e;
         if ((e = cudaStreamSynchronize(c->stream))) return e;
-        if (h[3] != 0 || h[0] > cap_task || h[1] > cap_chunk || h[2] > cap_blist) return cudaErrorUnknown;
+        if (h[3] != 0 || h[0] > A.cap_task || h[1] > A.cap_chunk || h[2] > A.cap_blist) return cudaErrorUnknown;
         ntask = h[0];
         nchunk = h[1];
         nblock = h[2];
         cur ^= 1;
     }
     if (nblock > 0)
-        RTSDF_LAUNCH(c, k_sah_block, (unsigned)nblock, SAH_THREADS, sizeof(BlockSmem), blist, ord0, ord1, pbox, order,
-                     bv.nodes, bv.leaf_parent, bv.root, counters);
+        RTSDF_LAUNCH(c, k_sah_block, (unsigned)nblock, SAH_THREADS, sizeof(BlockSmem), A.blist, A.ord0, A.ord1,
+                     A.pbox, order, L, A.counters);
     if ((e = cudaGetLastError())) return e;
     int32_t bad = 0;
-    if ((e = cudaMemcpyAsync(&bad, counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream))) return e;
+    if ((e = cudaMemcpyAsync(&bad, A.counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream))) return e;
     if ((e = cudaStreamSynchronize(c->stream))) return e;
     return bad ? cudaErrorUnknown : cudaSuccess;   // a capacity guard fired: cannot happen for a valid range
+}
+
+}  // namespace
+
+cudaError_t sah_topology(rtsdf_ctx* c, void* scratch, int32_t* order) {
+    Bvh& bv = c->bvh;
+    const int32_t n = (int32_t)bv.nt;
+    SahArena A;
+    cudaError_t e = carve(scratch, n, A);
+    if (!e) e = block_attr(c);
+    if (!e) e = cudaMemsetAsync(A.counters, 0, 16 * sizeof(int32_t), c->stream);
+    if (e) return e;
+    const int nch0 = (n + SAH_CH - 1) / SAH_CH;
+    const int init_threads = nch0 > SAH_BIN_WORDS ? nch0 : SAH_BIN_WORDS;
+    RTSDF_LAUNCH(c, k_sah_root, (unsigned)((init_threads + 255) / 256), 256, 0, A.tasks[0], A.chunks[0], A.bins[0],
+                 A.blist, n);
+    RTSDF_LAUNCH(c, k_sah_prims, (unsigned)((n + SAH_THREADS - 1) / SAH_THREADS), SAH_THREADS, 0, c->verts, c->tris,
+                 n, A.pbox, A.ord0, A.tasks[0]);
+    const Links L{bv.nodes, bv.leaf_parent, bv.root, nullptr, nullptr, nullptr};
+    return run_levels(c, A, L, order, n > SAH_CH ? 1 : 0, nch0, n > SAH_CH ? 0 : 1);
+}
+
+cudaError_t sah_segments(rtsdf_ctx* c, void* scratch, int32_t* order, const int32_t* order_in,
+                         const int32_t* bounds, int32_t nseg, int32_t* seg_root) {
+    Bvh& bv = c->bvh;
+    const int32_t n = (int32_t)bv.nt;
+    SahArena A;
+    cudaError_t e = carve(scratch, n, A);
+    if (!e) e = block_attr(c);
+    if (e) return e;
+    // the first level, laid out on the host
+    std::vector<SahTask> tasks;
+    std::vector<int4> chunks;
+    std::vector<SahRange> blist;
+    std::vector<int32_t> root0((size_t)nseg, 0);
+    for (int32_t k = 0; k < nseg; k++) {
+        const int32_t b = bounds[k], en = bounds[k + 1], m = en - b;
+        if (m == 1) {
+            root0[(size_t)k] = ~b;                // a one-triangle segment is its own leaf
+        } else if (m <= SAH_CH) {
+            blist.push_back(SahRange{b, en, -2 - k, 0});
+        } else {
+            SahTask t;
+            memset(&t, 0, sizeof(t));
+            t.b = b; t.e = en; t.parent = -2 - k; t.side = 0; t.buf = 0;
+            t.chunk0 = (int32_t)chunks.size();
+            t.nchunk = (m + SAH_CH - 1) / SAH_CH;
+            t.axis = -1; t.split = -1; t.child[0] = t.child[1] = -1;
+            for (int q = 0; q < t.nchunk; q++)
+                chunks.push_back(make_int4((int)tasks.size(), b + q * SAH_CH, std::min(SAH_CH, en - (b + q * SAH_CH)), 0));
+            tasks.push_back(t);
+        }
+    }
+    if ((int64_t)tasks.size() > A.cap_task || (int64_t)chunks.size() > A.cap_chunk ||
+        (int64_t)blist.size() > A.cap_blist)
+        return cudaErrorInvalidValue;   // cannot happen: the segments partition [0, n)
+    int32_t h0[16] = {0};
+    h0[2] = (int32_t)blist.size();
+    if ((e = cudaMemcpyAsync(A.counters, h0, sizeof(h0), cudaMemcpyHostToDevice, c->stream))) return e;
+    if ((e = cudaMemcpyAsync(seg_root, root0.data(), sizeof(int32_t) * (size_t)nseg, cudaMemcpyHostToDevice,
+                             c->stream)))
+        return e;
+    if (!tasks.empty() &&
+        ((e = cudaMemcpyAsync(A.tasks[0], tasks.data(), sizeof(SahTask) * tasks.size(), cudaMemcpyHostToDevice,
+                              c->stream)) ||
+         (e = cudaMemcpyAsync(A.chunks[0], chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice,
+                              c->stream))))
+        return e;
+    if (!blist.empty() && (e = cudaMemcpyAsync(A.blist, blist.data(), sizeof(SahRange) * blist.size(),
+                                               cudaMemcpyHostToDevice, c->stream)))
+        return e;
+    if ((e = cudaMemcpyAsync(A.ord0, order_in, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    RTSDF_LAUNCH(c, k_sah_prims, (unsigned)((n + SAH_THREADS - 1) / SAH_THREADS), SAH_THREADS, 0, c->verts, c->tris,
+                 n, A.pbox, (int32_t*)nullptr, (SahTask*)nullptr);
+    if (!tasks.empty())
+        RTSDF_LAUNCH(c, k_sah_task_init, (unsigned)tasks.size(), SAH_THREADS, 0, A.tasks[0], A.ord0, A.pbox, A.bins[0]);
+    // one-triangle segments are final at once
+    if ((e = cudaMemcpyAsync(order, order_in, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    const Links L{bv.nodes, bv.leaf_parent, bv.root, seg_root, nullptr, nullptr};
+    // the host vectors must outlive the copies above: run_levels synchronises
+    return run_levels(c, A, L, order, (int32_t)tasks.size(), (int32_t)chunks.size(), (int32_t)blist.size());
+}
+
+size_t sah_top_bytes(int32_t nseg) {
+    return 512 + sizeof(int32_t) * (size_t)nseg;   // counters | range | identity list
+}
+
+cudaError_t sah_top_prepare(rtsdf_ctx* c, void* scratch, int32_t nseg) {
+    if (nseg < 1 || nseg > SAH_CH) return cudaErrorInvalidValue;
+    std::vector<unsigned char> h(sah_top_bytes(nseg), 0);
+    SahRange r{0, nseg, -1, 0};
+    memcpy(h.data() + 256, &r, sizeof(r));
+    int32_t* list = (int32_t*)(h.data() + 512);
+    for (int32_t j = 0; j < nseg; j++) list[j] = j;
+    cudaError_t e = cudaMemcpyAsync(scratch, h.data(), h.size(), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);   // h is a local buffer
+    return e;
+}
+
+cudaError_t sah_top(rtsdf_ctx* c, void* scratch, int32_t nseg, const float4* boxes, const int32_t* node_ids,
+                    const int32_t* child_of) {
+    Bvh& bv = c->bvh;
+    if (nseg < 1 || nseg > SAH_CH) return cudaErrorInvalidValue;
+    if (nseg == 1) {
+        RTSDF_LAUNCH(c, k_sah_top_single, 1, 1, 0, child_of, bv.nodes, bv.leaf_parent, bv.root);
+        return cudaGetLastError();
+    }
+    cudaError_t e = block_attr(c);
+    if (e) return e;
+    unsigned char* p = (unsigned char*)scratch;
+    int32_t* counters = (int32_t*)p;
+    SahRange* range = (SahRange*)(p + 256);
+    int32_t* list = (int32_t*)(p + 512);
+    const Links L{bv.nodes, bv.leaf_parent, bv.root, nullptr, node_ids, child_of};
+    // counters, the range {0, nseg} and the identity list come from sah_top_prepare
+    RTSDF_LAUNCH(c, k_sah_block, 1, SAH_THREADS, sizeof(BlockSmem), range, list, list, boxes, (int32_t*)nullptr, L,
+                 counters);
+    return cudaGetLastError();
 }
 
 }  // namespace rtsdf

@@ -80,6 +80,18 @@ struct Bvh {
     int32_t *mv0 = nullptr, *mv1 = nullptr, *d_depth = nullptr;
     void* sah = nullptr;
     size_t sah_bytes = 0;
+    // two-level form (RTSDF_BVH_TWO_LEVEL): one subtree per object, kept
+    // across frames, under a top tree over the objects that every refit
+    // rebuilds
+    bool two_level = false;
+    int32_t top_n = 0;              // objects with triangles (listed in object order)
+    int32_t top_cap = 0;
+    int32_t* top_child = nullptr;   // [top_n] subtree of each listed object (node id or ~leaf)
+    int32_t* top_ids = nullptr;     // [top_n - 1] node ids of the top tree
+    float4* top_box = nullptr;      // [2 top_n] box (lo, hi) of each listed object
+    void* top_scratch = nullptr;    // sah_top's arena
+    int32_t* obj_count = nullptr;   // [n_obj] triangles per object (build scratch)
+    int32_t obj_cap = 0;
     int depth = 0;
     bool built = false;
 };
@@ -88,6 +100,20 @@ struct Bvh {
 // order[] (triangle at each leaf position) for nt >= 2.
 size_t sah_scratch_bytes(int64_t nt);
 cudaError_t sah_topology(rtsdf_ctx* c, void* scratch, int32_t* order);
+// One subtree per segment [bounds[k], bounds[k+1]) of the leaf positions
+// (order_in: triangle at each position; bounds: host [nseg + 1]); the
+// subtree of segment k is hooked at seg_root[k] (device), its root's parent
+// left negative.  order may not alias order_in.
+cudaError_t sah_segments(rtsdf_ctx* c, void* scratch, int32_t* order, const int32_t* order_in,
+                         const int32_t* bounds, int32_t nseg, int32_t* seg_root);
+// Top tree over 1 <= nseg <= 1024 subtrees: boxes (lo, hi per subtree),
+// node ids [nseg - 1], child_of [nseg]; hooks the subtrees' parents and the
+// root.  scratch: sah_top_bytes(nseg), prepared by sah_top_prepare.
+size_t sah_top_bytes(int32_t nseg);
+cudaError_t sah_top_prepare(rtsdf_ctx* c, void* scratch, int32_t nseg);
+cudaError_t sah_top(rtsdf_ctx* c, void* scratch, int32_t nseg, const float4* boxes, const int32_t* node_ids,
+                    const int32_t* child_of);
+constexpr int SAH_TOP_MAX = 1024;
 
 // Ring of event pairs per stage; summed (and emptied) by rtsdf_get_stats.
 constexpr int TIMER_RING = 128;

@@ -1,9 +1,11 @@
-"""BVH builders on the GPU.  Both topologies (binned SAH and Morton) must be
-binary trees over every triangle with the leaves in position order; the SAH
-tree must have the lower surface-area cost; the build must be deterministic;
-and the traced SDF must not depend on the builder (every ray keeps its
-closest hit, equal distances the smaller triangle index), so the two
-builders give bit-identical grids."""
+"""BVH builders on the GPU.  Every topology (binned SAH, Morton, two-level)
+must be a binary tree over every triangle, the one-tree builders with the
+leaves in position order; the SAH tree must have the lower surface-area
+cost; the build must be deterministic; a two-level tree must stay valid and
+close to a fresh SAH tree in cost as its objects move; and the traced SDF
+must not depend on the builder (every ray keeps its closest hit, equal
+distances the smaller triangle index), so all builders give bit-identical
+grids."""
 import numpy as np
 import pytest
 
@@ -42,13 +44,17 @@ def _build(mesh, builder, nc=16):
     rt.set_bvh_builder(builder)
     assert rt.get_bvh_builder() == builder
     rt.upload_mesh(mesh.verts, mesh.tris)
+    if mesh.vert_object is not None:
+        rt.set_objects(mesh.vert_object, mesh.n_objects)
     rt.build_bvh()
     return rt
 
 
-def _check_tree(ch, lt, root, nt):
-    """Every node and leaf reached once from the root; in-order leaves are
-    positions 0..nt-1; leaf_tri is a permutation of the triangles."""
+def _check_tree(ch, lt, root, nt, in_order=True):
+    """Every node and leaf reached once from the root; leaf_tri is a
+    permutation of the triangles; with in_order, the in-order leaves are
+    positions 0..nt-1 (the one-tree builders; a two-level tree orders its
+    objects by the top tree)."""
     assert np.array_equal(np.sort(lt), np.arange(nt))
     if nt < 2:
         assert root == -1
@@ -66,7 +72,9 @@ def _check_tree(ch, lt, root, nt):
         stack.append(int(ch[x, 1]))                        # right after left: left pops first
         stack.append(int(ch[x, 0]))
     assert seen.all()
-    assert order == list(range(nt))
+    assert sorted(order) == list(range(nt))
+    if in_order:
+        assert order == list(range(nt))
 
 
 def _sah_cost(ch, lt, root, mesh):
@@ -105,13 +113,13 @@ def _sah_cost(ch, lt, root, mesh):
     return float(area.sum() / area[root])
 
 
-@pytest.mark.parametrize("builder", ["sah", "lbvh"])
+@pytest.mark.parametrize("builder", ["sah", "lbvh", "two_level"])
 @pytest.mark.parametrize("scene", list(SCENES))
 def test_topology_is_a_tree_over_every_triangle(builder, scene):
     mesh = SCENES[scene]()
     rt = _build(mesh, builder)
     ch, lt, root = rt.bvh_topology()
-    _check_tree(ch, lt, root, mesh.tris.shape[0])
+    _check_tree(ch, lt, root, mesh.tris.shape[0], in_order=builder != "two_level")
     st = rt.stats()
     assert 1 <= st["bvh_depth"] <= mesh.tris.shape[0]
     rt.sync()
@@ -151,12 +159,44 @@ def test_identical_triangles_stay_shallow():
     rt.close()
 
 
+def _objects_scene():
+    # 40 spheres, one more object that is a single triangle, one without triangles
+    m = S.animated_scene(9, n_objects=40, n_lon=16, n_lat=9)
+    nv = m.verts.shape[0]
+    extra = np.array([[0.5, 0.5, 0.5], [0.52, 0.5, 0.5], [0.5, 0.53, 0.5]], np.float32)
+    verts = np.concatenate([m.verts, extra])
+    tris = np.concatenate([m.tris, np.array([[nv, nv + 1, nv + 2]], np.int32)])
+    vo = np.concatenate([m.vert_object, np.full(3, m.n_objects, np.int32)])
+    return S.Mesh(verts, tris, vo, m.n_objects + 2)
+
+
+def test_two_level_refit_keeps_a_valid_tree_of_sah_quality():
+    mesh = _objects_scene()
+    rt = _build(mesh, "two_level", nc=24)
+    nt = mesh.tris.shape[0]
+    verts = mesh.verts.copy()
+    for t in range(1, 6):
+        tr = S.object_translations(10, t, mesh.n_objects, 0.02).astype(np.float32)
+        rt.move_objects(tr)
+        rt.build_bvh(refit=True)
+        ch, lt, root = rt.bvh_topology()
+        _check_tree(ch, lt, root, nt, in_order=False)
+        verts = verts + tr[mesh.vert_object]             # the library's per-frame fp32 move
+        moved = S.Mesh(verts, mesh.tris, mesh.vert_object, mesh.n_objects)
+        two = _sah_cost(ch, lt, root, moved)
+        ref = _build(moved, "sah", nc=24)
+        fresh = _sah_cost(*ref.bvh_topology(), moved)
+        ref.close()
+        assert two <= 1.15 * fresh
+    rt.close()
+
+
 @pytest.mark.parametrize("refit", [False, True])
 def test_traced_sdf_does_not_depend_on_the_builder(refit):
     from paper_2210_04449_gb300 import RTSDF
     mesh = S.animated_scene(8, n_objects=6, n_lon=20, n_lat=11)
     out = {}
-    for b in ("sah", "lbvh"):
+    for b in ("sah", "lbvh", "two_level"):
         rt = RTSDF(24, seed=5)
         rt.set_bvh_builder(b)
         rt.upload_mesh(mesh.verts, mesh.tris)
@@ -173,3 +213,4 @@ def test_traced_sdf_does_not_depend_on_the_builder(refit):
         rt.close()
     for k in ("fine", "accum", "counts"):
         assert np.array_equal(out["sah"][k], out["lbvh"][k]), k
+        assert np.array_equal(out["sah"][k], out["two_level"][k]), k
