@@ -159,6 +159,20 @@ def test_identical_triangles_stay_shallow():
     rt.close()
 
 
+def test_two_level_falls_back_to_one_sah_tree():
+    # 1025 one-triangle objects: more than one top-tree block holds, so the
+    # build makes the single SAH tree (leaves in position order)
+    mesh = SCENES["1025"]()
+    rt = _build(mesh, "two_level")
+    ch, lt, root = rt.bvh_topology()
+    _check_tree(ch, lt, root, mesh.tris.shape[0], in_order=True)
+    ref = _build(mesh, "sah")
+    want = ref.bvh_topology()
+    assert np.array_equal(ch, want[0]) and np.array_equal(lt, want[1]) and root == want[2]
+    rt.close()
+    ref.close()
+
+
 def _objects_scene():
     # 40 spheres, one more object that is a single triangle, one without triangles
     m = S.animated_scene(9, n_objects=40, n_lon=16, n_lat=9)
