@@ -328,15 +328,16 @@ def run_gpu(args, rank, world):
 
 def time_shadow(rt, dev, reps=5):
     """Shadow forward (1920x1080), adjoint (1024x1024), jittered forward +
-    TAA resolve (1920x1080) and the resolve alone, on the context's fine SDF;
-    CUDA events over `reps` launches each."""
+    TAA resolve (1920x1080), the resolve alone, and the thin-surface
+    fallback (exact occlusion toward the light, 1920x1080), on the
+    context's fine SDF and BVH; CUDA events over `reps` launches each."""
     import torch
 
     from synth import scenes as S
     out = {}
     L = (0.4, 1.0, 0.3)
     for name, (w, h) in (("forward", (1920, 1080)), ("backward", (1024, 1024)),
-                         ("jittered_taa", (1920, 1080)), ("taa", (1920, 1080))):
+                         ("jittered_taa", (1920, 1080)), ("taa", (1920, 1080)), ("fallback", (1920, 1080))):
         pos, nrm = S.floor_gbuffer(w, h, y=0.02)
         pos_t, nrm_t = torch.tensor(pos, device=dev), torch.tensor(nrm, device=dev)
         vis = torch.empty((h, w), device=dev)
@@ -357,8 +358,12 @@ def time_shadow(rt, dev, reps=5):
                 rt.shadow(pos_t, nrm_t, L, k=8.0, steps=64, out=vis, jitter_vox=2.0, frame=frame[0])
                 rt.taa_resolve(vis, hist, 1.0 if frame[0] == 0 else 0.1)
                 frame[0] += 1
-            else:
+            elif name == "taa":
                 rt.taa_resolve(vis, hist, 0.1)
+            else:
+                rt.shadow_fallback(pos_t, nrm_t, L, vis.view(-1))
+        if name == "fallback":
+            rt.shadow(pos_t, nrm_t, L, k=8.0, steps=64, out=vis)
         once()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

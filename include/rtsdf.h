@@ -239,6 +239,23 @@ rtsdf_status rtsdf_shadow_jittered(rtsdf_t ctx, const float* sdf, const float* p
                                    float step_max_vox, float eps_vox, float jitter_vox, int32_t frame,
                                    float* vis);
 
+/* Sec. 3 (future work in the paper): thin-surface fallback.  The march can
+ * step through a surface thinner than its epsilon and leave holes in the
+ * umbra; the paper proposes shadow mapping in those regions.  Here: an
+ * exact occlusion test of the ray from the march's origin
+ * fmaf(nrm, 2 eps_vox h_f, pos) (fp32) along the unit light direction
+ * against the context's BVH (the tracer's box and ray/triangle tests; any
+ * hit at t >= 0 decides).  Blocked points get vis = 0 in place (vis: float32
+ * [npix] device, typically rtsdf_shadow's output; the others keep their
+ * value), and blocked (uint8 [npix] device, optional) receives 1 / 0.  The
+ * exact test only lowers visibility where the SDF missed an occluder: a
+ * thick occluder already stops the march (h < eps).  vis or blocked may be
+ * NULL, not both (RTSDF_E_ARG); eps_vox > 0 and a non-zero light as for
+ * rtsdf_shadow.  Needs a current BVH (RTSDF_E_STATE after moving objects
+ * until rtsdf_build_bvh).  Counted in the shadow stage. */
+rtsdf_status rtsdf_shadow_fallback(rtsdf_t ctx, const float* pos, const float* nrm, int64_t npix,
+                                   const float light[3], float eps_vox, float* vis, uint8_t* blocked);
+
 /* Sec. 2.3: temporal anti-aliasing of a visibility image for a static view.
  * cur: float32 [height x width] device, this frame (row-major); hist:
  * float32 [height x width] device, the resolved history, updated in place:

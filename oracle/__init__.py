@@ -96,6 +96,7 @@ def _load():
             "orc_shadow": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
                                   c_d, c_d, f64p, ctypes.c_void_p, ctypes.c_void_p]),
             "orc_shadow_jitter": (None, [c_u64, c_u32, c_i64, f64p]),
+            "orc_shadow_exact": (None, [f32p, i32p, c_i64, f32p, f32p, c_i64, f32p, c_f, i32p]),
             "orc_shadow_grad": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
                                        c_d, c_d, f64p, f64p, f64p]),
         }
@@ -461,6 +462,37 @@ def shadow(sdf, n, bmin, extent, pos, nrm, light_v, k, steps, step_max, eps, inf
     if info:
         return vis, inf.reshape(-1, 3)
     return vis
+
+
+def unit_light(light_v):
+    """The fp32 unit light direction: normalised in fp64 ((x^2 + y^2) + z^2,
+    then each component divided by the root), rounded to fp32."""
+    x, y, z = (float(np.float32(c)) for c in light_v)
+    nv = math.sqrt(x * x + y * y + z * z)
+    return np.array([x / nv, y / nv, z / nv], np.float32)
+
+
+def shadow_exact(verts, tris, pos, nrm, light_v, eps):
+    """Thin-surface fallback (Sec. 3: the march steps through surfaces
+    thinner than its epsilon and leaves holes in the umbra; the paper would
+    shadow-map those regions), read as an exact occlusion test toward the
+    light.  blocked[i] is True iff some triangle meets the ray from the
+    march's origin fmaf(nrm, 2 eps, pos) (fp32, one rounding) along the
+    fp32 unit light direction, by the tracer's fp32 ray/triangle test.
+    ``eps``: the march epsilon in world units (fp32)."""
+    v, t = _f32(verts), _i32(tris)
+    p, q = _f32(pos).reshape(-1, 3), _f32(nrm).reshape(-1, 3)
+    out = np.empty(p.shape[0], np.int32)
+    two_eps = float(np.float32(2.0) * np.float32(eps))
+    _load().orc_shadow_exact(v.reshape(-1), t.reshape(-1), t.shape[0], p.reshape(-1), q.reshape(-1),
+                             p.shape[0], unit_light(light_v), two_eps, out)
+    return out.astype(bool)
+
+
+def shadow_fallback(vis, blocked):
+    """Visibility after the thin-surface fallback: 0 where the exact test
+    is blocked, the march's value elsewhere (min(vis, 1 - blocked))."""
+    return np.where(np.asarray(blocked, bool), 0.0, np.asarray(vis, np.float64))
 
 
 def shadow_jitter(seed, frame, npix):

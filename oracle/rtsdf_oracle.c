@@ -777,6 +777,32 @@ EXPORT void orc_shadow(const float* sdf, int n, const double* bmin, double exten
     }
 }
 
+/* The thin-surface fallback of Sec. 3: where the march steps through a
+ * surface thinner than its epsilon, the umbra gets holes; the paper proposes
+ * shadow mapping in those regions.  Read here as an exact occlusion test
+ * toward the (directional) light from the march's own origin: blocked[i] = 1
+ * iff some triangle meets the ray o + t L, t >= 0, with
+ * o = fmaf(nrm, 2 eps, pos) in fp32 (the march's origin, single rounding),
+ * L the fp32 unit light direction, and the fp32 ray/triangle test of the
+ * tracer.  The shadow is then min(vis, 1 - blocked). */
+EXPORT void orc_shadow_exact(const float* verts, const int32_t* tris, int64_t nt, const float* pos,
+                             const float* nrm, int64_t npix, const float* L, float two_eps, int32_t* blocked)
+{
+    float* tv0 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    float* te1 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    float* te2 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    tri_edges(verts, tris, nt, tv0, te1, te2);
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < npix; i++) {
+        float o[3];
+        for (int a = 0; a < 3; a++) o[a] = fmaf(nrm[3 * i + a], two_eps, pos[3 * i + a]);
+        float t;
+        int f;
+        blocked[i] = closest_hit(o, L, tv0, te1, te2, nt, &t, &f) >= 0;
+    }
+    free(tv0); free(te1); free(te2);
+}
+
 /* Sec. 2.3 jitters each shadow ray's origin toward the light.  The fraction
  * xi in [0, 1) of pixel i in frame `frame` is the top 24 bits of the first
  * word of Philox-4x32-10 (Salmon et al., SC'11) with counter

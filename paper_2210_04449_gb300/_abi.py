@@ -71,6 +71,7 @@ SIGNATURES = {
     "rtsdf_shadow": (status_t, [ctx_t, c_vp, c_vp, c_vp, c_i64, F3, c_f, c_i32, c_f, c_f, c_vp]),
     "rtsdf_shadow_jittered": (status_t, [ctx_t, c_vp, c_vp, c_vp, c_i64, F3, c_f, c_i32, c_f, c_f, c_f, c_i32, c_vp]),
     "rtsdf_taa_resolve": (status_t, [ctx_t, c_vp, c_vp, c_i32, c_i32, c_f]),
+    "rtsdf_shadow_fallback": (status_t, [ctx_t, c_vp, c_vp, c_i64, F3, c_f, c_vp, c_vp]),
     "rtsdf_set_sign_mode": (status_t, [ctx_t, c_i32]),
     "rtsdf_get_sign_mode": (status_t, [ctx_t, ctypes.POINTER(c_i32)]),
     "rtsdf_set_bvh_builder": (status_t, [ctx_t, c_i32]),

@@ -199,6 +199,19 @@ class RTSDF:
                  int(steps), float(step_max_vox), float(eps_vox), vis.data_ptr())
         return vis
 
+    def shadow_fallback(self, pos, nrm, light, vis=None, eps_vox: float = 1.0, blocked=None):
+        """Thin-surface fallback: exact occlusion toward the light from the
+        march's origin; blocked points get ``vis`` = 0 in place.  ``blocked``
+        (uint8 [npix] device, optional) receives the occlusion flags."""
+        pos = pos.contiguous()
+        nrm = nrm.contiguous()
+        if vis is not None and not vis.is_contiguous():
+            raise ValueError("vis must be contiguous (it is updated in place)")
+        call("rtsdf_shadow_fallback", self._h, pos.data_ptr(), nrm.data_ptr(), pos.numel() // 3,
+             self._light3(light), float(eps_vox), vis.data_ptr() if vis is not None else None,
+             blocked.data_ptr() if blocked is not None else None)
+        return vis
+
     def taa_resolve(self, cur, hist, blend: float = 0.1):
         """In-place temporal anti-aliasing of ``hist`` [H, W] toward ``cur``."""
         if cur.dim() != 2 or tuple(cur.shape) != tuple(hist.shape) or not hist.is_contiguous():

@@ -436,6 +436,19 @@ rtsdf_status rtsdf_shadow_jittered(rtsdf_t c, const float* sdf, const float* pos
                                    jitter_vox * c->hf, frame, vis));
 }
 
+rtsdf_status rtsdf_shadow_fallback(rtsdf_t c, const float* pos, const float* nrm, int64_t npix, const float light[3],
+                                   float eps_vox, float* vis, uint8_t* blocked) {
+    float L[3], inv;
+    // k, steps, step_max are not used here: pass valid placeholders to the shared checks
+    rtsdf_status s = shadow_common(c, pos, nrm, npix, light, 1.f, 1, 1.f, eps_vox, L, &inv);
+    if (s != RTSDF_OK) return s;
+    if (npix > 0 && !vis && !blocked) return RTSDF_E_ARG;
+    if (!c->have_mesh || !c->bvh.built || c->bvh_dirty || c->bvh.nt != c->nt) return RTSDF_E_STATE;
+    DeviceGuard g(c->device);
+    StageTimer tm(c, ST_SHADOW);
+    return from_cuda(launch_shadow_exact(c, pos, nrm, npix, L, eps_vox * c->hf, vis, blocked));
+}
+
 rtsdf_status rtsdf_taa_resolve(rtsdf_t c, const float* cur, float* hist, int32_t width, int32_t height,
                                float blend) {
     if (!c || width < 0 || height < 0 || !(blend > 0.f && blend <= 1.f)) return RTSDF_E_ARG;

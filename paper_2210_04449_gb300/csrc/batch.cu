@@ -418,7 +418,8 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
                         setup_ray(ta, g - s_rp[scene], r);
                         // enter the scene's root in the concatenated tree
                         const SceneDesc& sd = b.sc[scene];
-                        r.node = ta.nt > 1 ? sd.wide_off : (ta.nt == 1 ? ~sd.tri_off : WIDE_EMPTY);
+                        r.node = ta.nt > 1 ? sd.wide_off : WIDE_EMPTY;
+                        r.leaf = ta.nt == 1 ? sd.tri_off : WIDE_EMPTY;
                         active = true;
                     }
                 }

@@ -232,6 +232,8 @@ cudaError_t launch_shadow(rtsdf_ctx* c, const float* sdf, const float* pos, cons
                           int64_t npix, const float L[3], float k, int steps, float smax,
                           float eps, float jitter, int frame, float* vis);
 cudaError_t launch_taa(rtsdf_ctx* c, const float* cur, float* hist, int w, int h, float blend);
+cudaError_t launch_shadow_exact(rtsdf_ctx* c, const float* pos, const float* nrm, int64_t npix, const float L[3],
+                                float eps, float* vis, uint8_t* blocked);
 cudaError_t launch_shadow_bwd(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm,
                               int64_t npix, const float L[3], float inv_norm, float k, int steps,
                               float smax, float eps, const float* dvis, float* dsdf,

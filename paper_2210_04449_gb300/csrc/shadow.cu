@@ -26,6 +26,7 @@
 // unnormalised light vector.  Points stopped by h < eps, points whose res
 // stayed 1 and clamped square roots carry no derivative.
 #include <math_constants.h>
+#include <string.h>
 
 #include "internal.cuh"
 #include "trace_dev.cuh"   // Philox-4x32-10
@@ -297,6 +298,47 @@ ShadowArgs make_args(rtsdf_ctx* c, const float* sdf, const float* pos, const flo
     return a;
 }
 
+// Thin-surface fallback (Sec. 3: the march can step through a surface
+// thinner than its epsilon and leave a hole in the umbra; the paper would
+// shadow-map such regions).  Exact occlusion of the ray from the march's
+// origin fmaf(n, 2 eps, p) along L: a BVH traversal that stops at the first
+// hit (any hit decides), with the tracer's box and ray/triangle tests.  A
+// blocked point gets visibility 0; the others keep the march's value.
+__global__ void __launch_bounds__(dev::TRACE_THREADS) k_shadow_exact(dev::TraceArgs t, const float* __restrict__ pos,
+                                                                     const float* __restrict__ nrm, long long npix,
+                                                                     float Lx, float Ly, float Lz, float two_eps,
+                                                                     float* vis, uint8_t* blocked) {
+    __shared__ int2 s_stack[dev::SMEM_STACK][dev::TRACE_THREADS];
+    int2 deep[TRACE_STACK - dev::SMEM_STACK];
+    dev::Stack stk{&s_stack[0][threadIdx.x], deep};
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= npix) return;                      // no barrier below
+    dev::Ray r;
+    r.o = make_float3(fmaf(nrm[3 * i], two_eps, pos[3 * i]), fmaf(nrm[3 * i + 1], two_eps, pos[3 * i + 1]),
+                      fmaf(nrm[3 * i + 2], two_eps, pos[3 * i + 2]));
+    r.d = make_float3(Lx, Ly, Lz);
+    r.id = make_float3(dev::safe_inv(Lx), dev::safe_inv(Ly), dev::safe_inv(Lz));
+    r.oid = make_float3(r.o.x * r.id.x, r.o.y * r.id.y, r.o.z * r.id.z);
+    r.bt = CUDART_INF_F;
+    r.bidx = 0x7FFFFFFF;
+    r.bfront = false;
+    r.node = t.nt > 1 ? 0 : WIDE_EMPTY;
+    r.leaf = t.nt == 1 ? 0 : WIDE_EMPTY;
+    r.sp = 0;
+    r.slot = 0;
+    r.steps = 0;
+    uint32_t nv = 0, ntest = 0;
+    // every step enters a node or tests a leaf (bounded by the node steps'
+    // own guard); the loop ends at the first hit or when nothing is left
+    while (r.bidx == 0x7FFFFFFF && !dev::ray_done(r)) {
+        dev::node_step<false>(t, r, stk, nv);
+        if (r.leaf != WIDE_EMPTY) dev::leaf_step<false>(t, r, stk, nv, ntest);
+    }
+    const bool b = r.bidx != 0x7FFFFFFF;
+    if (blocked) blocked[i] = (uint8_t)b;
+    if (b && vis) vis[i] = 0.f;
+}
+
 }  // namespace
 
 cudaError_t launch_shadow(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm, int64_t npix,
@@ -323,6 +365,20 @@ cudaError_t launch_taa(rtsdf_ctx* c, const float* cur, float* hist, int w, int h
     if (w == 0 || h == 0) return cudaSuccess;
     dim3 block(32, 8, 1), grid((unsigned)((w + 31) / 32), (unsigned)((h + 7) / 8), 1);
     RTSDF_LAUNCH(c, k_taa, grid, block, 0, cur, hist, w, h, blend);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow_exact(rtsdf_ctx* c, const float* pos, const float* nrm, int64_t npix, const float L[3],
+                                float eps, float* vis, uint8_t* blocked) {
+    if (npix == 0) return cudaSuccess;
+    dev::TraceArgs t;
+    memset(&t, 0, sizeof(t));
+    t.wide = c->bvh.wide;
+    t.tri = c->bvh.tri;
+    t.nt = c->bvh.nt;
+    t.err = c->d_err;
+    RTSDF_LAUNCH(c, k_shadow_exact, (unsigned)((npix + dev::TRACE_THREADS - 1) / dev::TRACE_THREADS),
+                 dev::TRACE_THREADS, 0, t, pos, nrm, (long long)npix, L[0], L[1], L[2], 2.f * eps, vis, blocked);
     return cudaGetLastError();
 }
 

@@ -174,8 +174,10 @@ __device__ __forceinline__ void setup_ray(const TraceArgs& a, uint64_t g, Ray& r
     r.bt = cap;
     r.bidx = 0x7FFFFFFF;
     r.bfront = false;
-    r.node = a.nt > 1 ? 0 : (a.nt == 1 ? ~0 : WIDE_EMPTY);   // no triangles: nothing to enter
-    r.leaf = WIDE_EMPTY;
+    // the root; a one-triangle mesh has no node, so its leaf starts parked
+    // (a ray with neither a node nor a parked leaf is done)
+    r.node = a.nt > 1 ? 0 : WIDE_EMPTY;
+    r.leaf = a.nt == 1 ? 0 : WIDE_EMPTY;
     r.sp = 0;
     r.slot = slot;
     r.steps = 0;

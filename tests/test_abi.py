@@ -52,6 +52,8 @@ def test_host_only_calls():
     assert lib.rtsdf_set_bvh_builder(None, 1) == 1
     assert lib.rtsdf_get_bvh_builder(None, None) == 1
     assert lib.rtsdf_get_bvh_topology(None, None, None, None) == 1
+    from paper_2210_04449_gb300._abi import F3
+    assert lib.rtsdf_shadow_fallback(None, None, None, 0, F3(0.0, 1.0, 0.0), 1.0, None, None) == 1
     cfg = _abi.Config()
     cfg.extent = 1.0
     cfg.coarse_n = 300          # above the 256 limit

@@ -230,3 +230,70 @@ def test_taa_resolve_rules():
     mx = np.max([pad[dy:dy + H, dx:dx + W] for dy in range(3) for dx in range(3)], axis=0)
     inside = (cur + 0.01 <= mx)            # pixels whose first history was not clamped
     assert np.allclose((h - cur)[inside], (0.9 ** 6 * d0)[inside], rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- thin-surface fallback (Sec. 3)
+
+def _one_triangle(z=1.0):
+    v = np.array([[0.0, 0.0, z], [1.0, 0.0, z], [0.0, 1.0, z]], np.float32)
+    return v, np.array([[0, 1, 2]], np.int32)
+
+
+@pytest.mark.parametrize("light", [(0.0, 0.0, 1.0), (0.3, -0.2, 1.0), (-0.5, 0.4, 0.8)])
+def test_exact_occlusion_closed_form(light):
+    # floor points below the triangle x, y >= 0, x + y <= 1 at z = 1: the ray
+    # toward L meets z = 1 at (x, y) + (1 - oz) (Lx, Ly) / Lz; blocked iff that
+    # point is inside the triangle (points within 1e-3 of an edge skipped)
+    v, t = _one_triangle()
+    rng = np.random.default_rng(3)
+    pos = np.zeros((4000, 3), np.float32)
+    pos[:, :2] = rng.uniform(-0.6, 1.4, (4000, 2)).astype(np.float32)
+    nrm = np.tile(np.array([0.0, 0.0, 1.0], np.float32), (4000, 1))
+    eps = np.float32(0.01)
+    blocked = oracle.shadow_exact(v, t, pos, nrm, light, eps)
+    L = np.asarray(light, np.float64) / np.linalg.norm(light)
+    oz = 2.0 * float(eps)
+    hx = pos[:, 0].astype(np.float64) + (1.0 - oz) * L[0] / L[2]
+    hy = pos[:, 1].astype(np.float64) + (1.0 - oz) * L[1] / L[2]
+    margin = np.minimum(np.minimum(hx, hy), 1.0 - hx - hy)
+    clear = np.abs(margin) > 1e-3
+    assert clear.sum() > 3500
+    np.testing.assert_array_equal(blocked[clear], (margin > 0)[clear])
+    assert 0 < blocked.sum() < blocked.size
+
+
+def test_exact_occlusion_only_ahead_of_the_origin():
+    # a light below the floor points away from the triangle: nothing blocks;
+    # a triangle below the origin never blocks a ray going up
+    v, t = _one_triangle(z=1.0)
+    pos = np.array([[0.2, 0.2, 0.0], [0.1, 0.3, 0.0]], np.float32)
+    nrm = np.tile(np.array([0.0, 0.0, 1.0], np.float32), (2, 1))
+    assert not oracle.shadow_exact(v, t, pos, nrm, (0.0, 0.0, -1.0), 0.01).any()
+    assert oracle.shadow_exact(v, t, pos, nrm, (0.0, 0.0, 1.0), 0.01).all()
+    vb, tb = _one_triangle(z=-0.5)
+    assert not oracle.shadow_exact(vb, tb, pos, nrm, (0.0, 0.0, 1.0), 0.01).any()
+
+
+def test_exact_occlusion_is_the_any_hit_of_cast_rays():
+    # the same decision as the tracer's closest-hit cast from the march origin
+    m = S.random_soup(12, 300)
+    rng = np.random.default_rng(4)
+    pos = rng.uniform(0.0, 1.0, (500, 3)).astype(np.float32)
+    nrm = rng.normal(size=(500, 3)).astype(np.float32)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    eps = np.float32(2.0 ** -8)
+    blocked = oracle.shadow_exact(m.verts, m.tris, pos, nrm, (0.2, 1.0, 0.4), eps)
+    L = oracle.unit_light((0.2, 1.0, 0.4))
+    # 2 eps is a power of two, so n * 2 eps is exact in fp32 and the fp64 sum
+    # of two fp32 values this close in magnitude is exact: rounding it once to
+    # fp32 is fmaf(n, 2 eps, p)
+    o = (pos.astype(np.float64) + nrm.astype(np.float64) * (2.0 * float(eps))).astype(np.float32)
+    tout, _, tri = oracle.cast_rays(m.verts, m.tris, o, np.tile(L, (500, 1)))
+    np.testing.assert_array_equal(blocked, tri >= 0)
+    assert 0 < blocked.sum() < blocked.size
+
+
+def test_fallback_takes_the_umbra_only_where_blocked():
+    vis = np.array([0.0, 0.3, 1.0, 0.7])
+    blocked = np.array([True, True, False, False])
+    np.testing.assert_array_equal(oracle.shadow_fallback(vis, blocked), [0.0, 0.0, 1.0, 0.7])
