@@ -51,8 +51,8 @@ FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
     # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant" (1 pass), SAH tree:
-    # 11.05 GB + 176.3 MB
-    "1135b1eb3fdbf31a": 11.0515e9 + 176.32e6,
+    # 11.17 GB + 178.7 MB
+    "be3e97993857e9f4": 11.1687e9 + 178.67e6,
 }
 TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 
