@@ -288,12 +288,10 @@ def run_gpu(args, rank, world):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded procedural scene: 500 displaced UV spheres, random rigid motion)",
-        "config": {"workload": f"animated {nc}^3->{2 * nc}^3, {mesh.n_objects} spheres / {mesh.nt:,} tris, "
-                               "64 rays/texel, d=2 voxels, beta=0.5, reset in changed regions, "
-                               f"per-frame BVH {args.bvh} ({args.builder})+voxelize+JFA",
-                   "coarse_n": nc, "fine_n": 2 * nc, "triangles": int(mesh.nt), "rays_per_texel": RAYS,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": f"inputs larger than L2 (fine grids 3 x {(2 * nc) ** 3 * 4 >> 20} MB)"},
+        "config": dict(workload_config(nc, mesh.n_objects, mesh.nt),
+                       bvh=f"per-frame {args.bvh} ({args.builder})",
+                       parallelism="replicas" if world > 1 else "single GPU",
+                       l2=f"inputs larger than L2 (fine grids 3 x {(2 * nc) ** 3 * 4 >> 20} MB)"),
         "gpu_launches": int(launches),
         "rays_per_s": round(rays_frame / (trace_ms * 1e-3)) if trace_ms else None,
         "masked_texels": int(n_masked_tex),
@@ -500,6 +498,14 @@ def run_batched(dev, frames=3, rays=32, d_vox=2.0):
 
 
 # ----------------------------------------------------------------- CPU oracle
+def workload_config(nc, n_objects, n_tris):
+    """The benchmark workload, named by what it is (both arms report it)."""
+    return {"workload": f"animated {nc}^3->{2 * nc}^3, {n_objects} spheres / {n_tris:,} tris, "
+                        f"{RAYS} rays/texel, d={D_VOX:g} voxels, beta={BETA:g}, reset in changed regions, "
+                        "per frame: move, BVH, voxelize, JFA, mask, trace",
+            "coarse_n": nc, "fine_n": 2 * nc, "triangles": int(n_tris), "rays_per_texel": RAYS}
+
+
 def oracle_frame_sample(n_texels, seed=SEED, objects=N_OBJ, masked_texels=None):
     """Time the oracle (as it stands) on one frame of the same workload:
     voxelize + jump flood + mask in full, brute-force tracing of n_texels
@@ -532,7 +538,8 @@ def oracle_frame_sample(n_texels, seed=SEED, objects=N_OBJ, masked_texels=None):
     total = (t1 - t0) + (t2 - t1) + (t3 - t2) + per_texel * m_tex
     return total * 1e3, {"voxelize_s": round(t1 - t0, 3), "jfa_s": round(t2 - t1, 3), "mask_s": round(t3 - t2, 3),
                          "trace_s_per_texel": round(per_texel, 4), "texels_sampled": int(pick.size),
-                         "masked_texels": int(m_tex), "sample_cpu_s": round(t5 - t0, 2)}
+                         "masked_texels": int(m_tex), "sample_cpu_s": round(t5 - t0, 2),
+                         "triangles": int(mesh.nt)}
 
 
 def oracle_threads():
@@ -556,7 +563,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": "animated 256^3->512^3, 500 spheres / 1,000,000 tris, 64 rays/texel"},
+            "config": dict(workload_config(NC, N_OBJ, info["triangles"]), parallelism="host cores"),
             "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                              "sample": f"per step: one frame's voxelize + JFA + mask in full, brute-force trace "
                                        f"of {info['texels_sampled']} masked texels x {RAYS} rays over all "
