@@ -228,3 +228,20 @@ def test_traced_sdf_does_not_depend_on_the_builder(refit):
     for k in ("fine", "accum", "counts"):
         assert np.array_equal(out["sah"][k], out["lbvh"][k]), k
         assert np.array_equal(out["sah"][k], out["two_level"][k]), k
+
+
+def test_full_size_sah_tree():
+    # the benchmark scene: the SAH tree is a tree over all 1,000,000
+    # triangles with the leaves in position order, and cheaper than the
+    # Morton tree by the surface-area cost
+    mesh = S.animated_scene(2, n_objects=500)
+    costs = {}
+    for b in ("sah", "lbvh"):
+        rt = _build(mesh, b, nc=64)
+        ch, lt, root = rt.bvh_topology()
+        if b == "sah":
+            _check_tree(ch, lt, root, mesh.tris.shape[0])
+        costs[b] = _sah_cost(ch, lt, root, mesh)
+        rt.close()
+    assert costs["sah"] < 0.95 * costs["lbvh"]
+

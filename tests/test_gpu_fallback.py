@@ -165,3 +165,29 @@ def test_trace_with_one_or_two_triangles(n_tris):
     assert np.max(np.abs(u[fin] - pipe.u[fin]), initial=0.0) <= 2e-5 * np.sqrt(3.0)
     assert np.array_equal(cnt & 0xFFFF, pipe.nF) and np.array_equal(cnt >> 16, pipe.nB)
     rt.close()
+
+
+def test_full_size_flags_sampled():
+    # the benchmark scene (500 spheres, 1,000,000 triangles) and a 1920x1080
+    # floor G-buffer: every flag from the GPU, 512 sampled points from the
+    # oracle's brute-force test over all triangles
+    import torch
+    from paper_2210_04449_gb300 import RTSDF
+    mesh = S.animated_scene(2, n_objects=500)
+    rt = RTSDF(256, seed=2)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.build_bvh()
+    pos, nrm = S.floor_gbuffer(1920, 1080, y=0.02)
+    pos, nrm = pos.reshape(-1, 3), nrm.reshape(-1, 3)
+    light = (0.4, 1.0, 0.3)
+    tp, tn = torch.tensor(pos, device=rt.device), torch.tensor(nrm, device=rt.device)
+    blocked = torch.zeros(pos.shape[0], device=rt.device, dtype=torch.uint8)
+    rt.shadow_fallback(tp, tn, light, None, blocked=blocked)
+    rt.sync()
+    b = blocked.cpu().numpy().astype(bool)
+    pick = np.random.default_rng(5).choice(pos.shape[0], 512, replace=False)
+    eps = np.float32(1.0) * (np.float32(1.0) / np.float32(512))
+    want = oracle.shadow_exact(mesh.verts, mesh.tris, pos[pick], nrm[pick], light, eps)
+    assert np.array_equal(b[pick], want)
+    assert 0.05 < b.mean() < 0.95
+    rt.close()
