@@ -129,3 +129,31 @@ def test_batch_nearest_face_variant_equals_sequential():
             assert np.array_equal(got[k], want[k]), (i, k)
         rt.close()
     b.close()
+
+
+def test_batch_with_any_builder_and_a_one_triangle_scene():
+    # scenes built by every builder (the animated one two-level, over its
+    # objects) plus a scene of a single triangle: the grids of plain frames
+    from paper_2210_04449_gb300 import RTSDFBatch
+    one = S.Mesh(np.array([[0.3, 0.4, 0.3], [0.7, 0.45, 0.35], [0.4, 0.5, 0.7]], np.float32),
+                 np.array([[0, 1, 2]], np.int32))
+    items = _workload() + [(dict(coarse_n=16, beta_vox=0.5, seed=8), one)]
+    d, R, frames = 2.0, 8, [0, 1]
+    b = RTSDFBatch([cfg for cfg, _ in items])
+    builders = ["sah", "lbvh", "two_level", "lbvh", "sah", "two_level", "two_level", "sah"]
+    for i, (sc, (_, mesh)) in enumerate(zip(b.scenes, items)):
+        sc.set_bvh_builder(builders[i])
+        sc.upload_mesh(mesh.verts, mesh.tris)
+        if mesh.vert_object is not None and mesh.n_objects > 0:
+            sc.set_objects(mesh.vert_object, mesh.n_objects)
+        sc.build_bvh()
+    for f in frames:
+        b.frame(d, R, f)
+    b.sync()
+    ref = _run_plain(items, frames, d, R)
+    for i, sc in enumerate(b.scenes):
+        got = _grids(sc)
+        for k in ("seeds", "accum", "counts", "fine", "masked"):
+            assert np.array_equal(got[k], ref[i][k]), (i, k)
+    assert (ref[-1]["counts"] != 0).any()                  # the one-triangle scene was hit
+    b.close()

@@ -57,6 +57,7 @@ def test_calls_out_of_order():
     m = S.animated_scene(3, n_objects=4, n_lon=12, n_lat=7)
     rt = RTSDF(16)
     assert _name(rt.voxelize) == "RTSDF_E_STATE"         # no mesh yet
+    assert _name(rt.bvh_topology) == "RTSDF_E_STATE"     # no BVH yet
     rt.upload_mesh(m.verts, m.tris)
     assert _name(rt.jfa) == "RTSDF_E_STATE"              # before voxelize
     assert _name(rt.build_bvh, refit=True) == "RTSDF_E_STATE"   # refit before a build
@@ -102,6 +103,9 @@ def test_argument_checks():
     assert _name(rt.taa_resolve, img, img, 0.1) == "RTSDF_E_ARG"           # cur and hist overlap
     assert _name(rt.taa_resolve, img.clone(), img, 0.0) == "RTSDF_E_ARG"   # blend outside (0, 1]
     assert _name(rt.set_tuning, refill_min=0) == "RTSDF_E_ARG"
+    from paper_2210_04449_gb300 import _abi
+    assert _abi.lib().rtsdf_set_bvh_builder(rt._h, 7) == 1                 # unknown builder
+    assert rt.get_bvh_builder() == "sah"
     assert _name(rt.set_tuning, jfa_tile=9) == "RTSDF_E_ARG"
     state = rt.save_state()
     assert _name(rt.load_state, state[:-1]) == "RTSDF_E_ARG"              # truncated
