@@ -107,16 +107,19 @@ def test_room_sampled_texels():
     _compare(rt, pipe, sample, "room sample")
 
 
-def test_full_size_animated_frames_sampled_texels():
+@pytest.mark.parametrize("builder,refit", [("sah", False), ("two_level", True)])
+def test_full_size_animated_frames_sampled_texels(builder, refit):
     # the benchmark workload: 500 displaced spheres (1,000,000 triangles),
     # 256^3 -> 512^3, 64 rays per texel, every object moved before the second
-    # frame (refit, re-voxelize, JFA, reset), in the autotuned launch
-    # configuration the benchmark times; 96 fine texels sampled from the
-    # masked ones are traced by the oracle by brute force over all triangles
+    # frame (BVH rebuild -- or the two-level refit --, re-voxelize, JFA,
+    # reset), in the autotuned launch configuration the benchmark times; 96
+    # fine texels sampled from the masked ones are traced by the oracle by
+    # brute force over all triangles
     from paper_2210_04449_gb300 import RTSDF
     mesh = S.animated_scene(2, n_objects=500)
     nc, d, beta, R, seed = 256, 2.0, 0.5, 64, 2
     rt = RTSDF(nc, beta_vox=beta, seed=seed)
+    rt.set_bvh_builder(builder)
     rt.upload_mesh(mesh.verts, mesh.tris)
     rt.set_objects(mesh.vert_object, mesh.n_objects)
     rt.build_bvh()
@@ -133,11 +136,11 @@ def test_full_size_animated_frames_sampled_texels():
     mv = np.any(tr != 0, axis=1)
     verts1 = (mesh.verts + tr[mesh.vert_object]).astype(np.float32)
     rt.move_objects(tr)
-    rt.build_bvh(refit=True)
+    rt.build_bvh(refit=refit)
     rt.update(d, R, 1)
     pipe.frame(verts1, mesh.tris, 1, R, moved_aabbs=(lo[mv], hi[mv]))
     rt.sync()
-    exact = _compare(rt, pipe, sample, "animated 1M full size sample")
+    exact = _compare(rt, pipe, sample, f"animated 1M full size sample ({builder}, refit={refit})")
     assert exact == 1.0
 
 
