@@ -72,8 +72,10 @@ def test_empty_scene():
 
 @pytest.mark.parametrize("nc", [128, 256])
 def test_full_size_room_and_sphere_cloud(nc):
-    # the largest coarse grids of the workloads: bit-exact voxels and seeds
-    m = S.room_scene(1) if nc == 128 else S.animated_scene(2, n_objects=120)
+    # the coarse grids of the workloads (the 256^3 one is the benchmark scene,
+    # 1,000,000 triangles): bit-exact voxels and seeds under every pass
+    # kernel, and the coarse SDF of the last pass
+    m = S.room_scene(1) if nc == 128 else S.animated_scene(2, n_objects=500)
     rt = _ctx(nc)
     rt.upload_mesh(m.verts, m.tris)
     rt.voxelize()
@@ -87,6 +89,11 @@ def test_full_size_room_and_sphere_cloud(nc):
         rt.jfa()
         seeds_g = seeds_to_linear(rt.grids()["seeds"].cpu().numpy(), nc)
         assert np.array_equal(seeds_g, seeds_o), tile
+    c_g = rt.grids()["coarse"].cpu().numpy().astype(np.float64)
+    c_o = oracle.coarse_sdf(seeds_o, nc, 1.0, 0.5)
+    fin = np.isfinite(c_o)
+    assert np.array_equal(fin, np.isfinite(c_g))
+    assert np.max(np.abs(c_g[fin] - c_o[fin])) <= 1e-6
     rt.sync()
 
 
