@@ -90,7 +90,10 @@ def _load():
             "orc_texel_centre": (None, [f32p, c_f, c_int, c_i64, f32p]),
             "orc_trace": (None, [f32p, i32p, c_i64, f32p, c_f, c_int, c_u64, c_int, c_int,
                                  i64p, c_i64, f32p, i32p, i32p, i64p, i32p]),
+            "orc_trace_bvh": (None, [f32p, i32p, c_i64, f32p, c_f, c_int, c_u64, c_int, c_int,
+                                     i64p, c_i64, f32p, i32p, i32p, i64p, i32p]),
             "orc_cast_rays": (None, [f32p, i32p, c_i64, f32p, f32p, c_i64, f32p, i32p, i64p]),
+            "orc_cast_rays_bvh": (None, [f32p, i32p, c_i64, f32p, f32p, c_i64, f32p, i32p, i64p]),
             "orc_point_mesh_distance": (None, [f32p, i32p, c_i64, f64p, c_i64, f64p]),
             "orc_sample": (c_d, [f32p, c_int, f64p, c_d, f64p]),
             "orc_shadow": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
@@ -264,10 +267,17 @@ def texel_centre(bmin, extent, nf, j):
     return o
 
 
-def trace(verts, tris, bmin, extent, nf, seed, frame, R, texels, nearest=False):
+def trace(verts, tris, bmin, extent, nf, seed, frame, R, texels, nearest=False, accel="brute"):
     """One frame of Sec. 2.2 tracing for the given fine texels: (r_t fp32,
     #front, #back, triangle of r_t), plus with ``nearest`` the face of the
-    nearest hit (1 = back; on equal distances a front hit wins)."""
+    nearest hit (1 = back; on equal distances a front hit wins).
+
+    ``accel``: "brute" tests every ray against every triangle (the
+    definition); "bvh" finds the same closest hits through a bounding-volume
+    hierarchy that only skips triangles a ray cannot reach before its best
+    hit (same fp32 test and tie rule; pinned bit for bit to "brute")."""
+    if accel not in ("brute", "bvh"):
+        raise ValueError(accel)
     v, t = _f32(verts), _i32(tris)
     tx = np.ascontiguousarray(texels, dtype=np.int64)
     m = tx.size
@@ -276,22 +286,27 @@ def trace(verts, tris, bmin, extent, nf, seed, frame, R, texels, nearest=False):
     nb = np.empty(m, np.int32)
     bt = np.empty(m, np.int64)
     rb = np.empty(m, np.int32)
-    _load().orc_trace(v.reshape(-1), t.reshape(-1), t.shape[0], _f32(bmin), extent, nf,
-                      int(seed) & (2 ** 64 - 1), frame, R, tx, m, r, nf_, nb, bt, rb)
+    fn = _load().orc_trace if accel == "brute" else _load().orc_trace_bvh
+    fn(v.reshape(-1), t.reshape(-1), t.shape[0], _f32(bmin), extent, nf,
+       int(seed) & (2 ** 64 - 1), frame, R, tx, m, r, nf_, nb, bt, rb)
     if nearest:
         return r, nf_, nb, bt, rb
     return r, nf_, nb, bt
 
 
-def cast_rays(verts, tris, orig, dirs):
+def cast_rays(verts, tris, orig, dirs, accel="brute"):
+    """Closest hit of arbitrary rays: (t fp32, +inf on a miss; front face;
+    triangle index or -1).  ``accel`` as in :func:`trace`."""
+    if accel not in ("brute", "bvh"):
+        raise ValueError(accel)
     v, t = _f32(verts), _i32(tris)
     o, d = _f32(orig).reshape(-1, 3), _f32(dirs).reshape(-1, 3)
     n = o.shape[0]
     tout = np.empty(n, np.float32)
     fr = np.empty(n, np.int32)
     tri = np.empty(n, np.int64)
-    _load().orc_cast_rays(v.reshape(-1), t.reshape(-1), t.shape[0], o.reshape(-1), d.reshape(-1),
-                          n, tout, fr, tri)
+    fn = _load().orc_cast_rays if accel == "brute" else _load().orc_cast_rays_bvh
+    fn(v.reshape(-1), t.reshape(-1), t.shape[0], o.reshape(-1), d.reshape(-1), n, tout, fr, tri)
     return tout, fr.astype(bool), tri
 
 
@@ -370,13 +385,17 @@ class FinePipeline:
     c and restart their accumulator; masked tracked texels may be reset
     (moved objects), then are traced and updated by Eq. 1."""
 
-    def __init__(self, bmin, extent, nc, beta_vox, d_vox, alpha, seed, track=None, sign="vote"):
+    def __init__(self, bmin, extent, nc, beta_vox, d_vox, alpha, seed, track=None, sign="vote", accel="brute"):
         """sign: "vote" (Sec. 2.2: negative when back-face hits outnumber
         front-face hits, counts kept over frames) or "nearest" (the variant
         that keeps the face of the nearest hit found so far; on equal
-        distances a front hit wins)."""
+        distances a front hit wins).  accel: how :func:`trace` finds the
+        closest hits ("brute" or "bvh", same results)."""
         if sign not in ("vote", "nearest"):
             raise ValueError(sign)
+        if accel not in ("brute", "bvh"):
+            raise ValueError(accel)
+        self.accel = accel
         self.bmin = np.asarray(bmin, np.float32)
         self.extent = float(extent)
         self.nc, self.nf = nc, 2 * nc
@@ -418,7 +437,7 @@ class FinePipeline:
             self.back[sel[rs]] = 0
         if sel.size:
             r, cf, cb, _, rb = trace(verts, tris, self.bmin, self.extent, self.nf, self.seed, frame, R, tx[sel],
-                                     nearest=True)
+                                     nearest=True, accel=self.accel)
             if self.sign == "vote":
                 self.u[sel] = eq1_update(self.u[sel], cpar[sel], r, self.alpha)
                 self.nF[sel] += cf

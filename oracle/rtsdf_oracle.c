@@ -567,6 +567,268 @@ EXPORT void orc_cast_rays(const float* verts, const int32_t* tris, int64_t nt, c
 }
 
 /* ======================================================================
+ * Sec. 2.2 -- the same closest hit, found faster (for whole-frame checks).
+ * A bounding-volume hierarchy only skips triangles that a ray cannot reach
+ * before its best hit; every triangle it does test goes through the same
+ * fp32 ray_tri_f32 and the same (t, then smaller index) rule, so the result
+ * is the brute-force closest_hit's.  Build: median split (by centroid,
+ * fp64, ties by triangle index) along the longest axis of the centroid
+ * bounds, leaves of at most ORC_LEAF triangles.  Boxes are fp64 over the
+ * fp32 vertices, widened by ORC_PAD on every side, and a box is entered
+ * when the ray's fp64 slab interval meets [0, best t + ORC_PAD]; the pad
+ * keeps a triangle that fp32 rounding accepts slightly outside its exact
+ * extent (a grazing hit) from being skipped.  The tests compare this path
+ * with the brute-force one bit for bit.
+ * ====================================================================== */
+
+#define ORC_LEAF 4
+#define ORC_PAD 1e-4
+
+typedef struct {
+    double lo[3], hi[3];
+    int64_t left, right;      /* children (internal) or -1 */
+    int64_t first, count;     /* leaf: range of the index array */
+} obvh_node;
+
+typedef struct {
+    obvh_node* nodes;
+    int64_t n_nodes;
+    int64_t* idx;             /* triangle index per leaf slot */
+    double* cen;              /* centroid [nt][3] */
+    const float* tv0; const float* te1; const float* te2;
+    const float* verts; const int32_t* tris;
+} obvh;
+
+static double cen_key(const obvh* b, int64_t i, int ax) { return b->cen[3 * i + ax]; }
+
+/* strict order on (centroid along ax, triangle index) */
+static int cen_less(const obvh* b, int64_t i, int64_t j, int ax)
+{
+    double a = cen_key(b, i, ax), c = cen_key(b, j, ax);
+    return a < c || (a == c && i < j);
+}
+
+/* quickselect: reorder idx[lo..hi) so that idx[k] is the k-th smallest and
+ * every element before it is smaller */
+static void select_k(const obvh* b, int64_t* idx, int64_t lo, int64_t hi, int64_t k, int ax)
+{
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        /* median of three as the pivot */
+        int64_t a = idx[lo], m = idx[mid], z = idx[hi - 1], pv;
+        if (cen_less(b, a, m, ax)) pv = cen_less(b, m, z, ax) ? m : (cen_less(b, a, z, ax) ? z : a);
+        else pv = cen_less(b, a, z, ax) ? a : (cen_less(b, m, z, ax) ? z : m);
+        int64_t i = lo, j = hi - 1;
+        while (i <= j) {
+            while (cen_less(b, idx[i], pv, ax)) i++;
+            while (cen_less(b, pv, idx[j], ax)) j--;
+            if (i <= j) { int64_t t = idx[i]; idx[i] = idx[j]; idx[j] = t; i++; j--; }
+        }
+        if (k <= j) hi = j + 1;
+        else if (k >= i) lo = i;
+        else return;
+    }
+}
+
+static void obvh_box(const obvh* b, int64_t first, int64_t count, double* lo, double* hi)
+{
+    for (int a = 0; a < 3; a++) { lo[a] = INFINITY; hi[a] = -INFINITY; }
+    for (int64_t s = first; s < first + count; s++) {
+        int64_t t = b->idx[s];
+        for (int v = 0; v < 3; v++) {
+            const float* p = b->verts + 3 * (int64_t)b->tris[3 * t + v];
+            for (int a = 0; a < 3; a++) {
+                if ((double)p[a] < lo[a]) lo[a] = p[a];
+                if ((double)p[a] > hi[a]) hi[a] = p[a];
+            }
+        }
+    }
+    for (int a = 0; a < 3; a++) { lo[a] -= ORC_PAD; hi[a] += ORC_PAD; }
+}
+
+static int64_t obvh_build_rec(obvh* b, int64_t first, int64_t count)
+{
+    int64_t id = b->n_nodes++;
+    obvh_node* nd = &b->nodes[id];
+    obvh_box(b, first, count, nd->lo, nd->hi);
+    nd->first = first;
+    nd->count = count;
+    nd->left = nd->right = -1;
+    if (count <= ORC_LEAF) return id;
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t s = first; s < first + count; s++)
+        for (int a = 0; a < 3; a++) {
+            double c = cen_key(b, b->idx[s], a);
+            if (c < clo[a]) clo[a] = c;
+            if (c > chi[a]) chi[a] = c;
+        }
+    int ax = 0;
+    for (int a = 1; a < 3; a++) if (chi[a] - clo[a] > chi[ax] - clo[ax]) ax = a;
+    int64_t half = count / 2;
+    select_k(b, b->idx, first, first + count, first + half, ax);
+    int64_t l = obvh_build_rec(b, first, half);
+    int64_t r = obvh_build_rec(b, first + half, count - half);
+    b->nodes[id].left = l;   /* nodes[] does not move: sized up front */
+    b->nodes[id].right = r;
+    return id;
+}
+
+static void obvh_build(obvh* b, const float* verts, const int32_t* tris, int64_t nt,
+                       const float* tv0, const float* te1, const float* te2)
+{
+    b->verts = verts; b->tris = tris; b->tv0 = tv0; b->te1 = te1; b->te2 = te2;
+    b->nodes = (obvh_node*)malloc(sizeof(obvh_node) * (size_t)(2 * (nt > 0 ? nt : 1)));
+    b->idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
+    b->cen = (double*)malloc(sizeof(double) * 3 * (size_t)(nt > 0 ? nt : 1));
+    b->n_nodes = 0;
+    for (int64_t i = 0; i < nt; i++) {
+        b->idx[i] = i;
+        for (int a = 0; a < 3; a++) {
+            double s = 0;
+            for (int v = 0; v < 3; v++) s += verts[3 * (int64_t)tris[3 * i + v] + a];
+            b->cen[3 * i + a] = s / 3.0;
+        }
+    }
+    if (nt > 0) obvh_build_rec(b, 0, nt);
+}
+
+static void obvh_free(obvh* b) { free(b->nodes); free(b->idx); free(b->cen); }
+
+/* Entry distance of the ray (fp64, origin o, reciprocal direction inv;
+ * inv = +-inf on a zero component) into the box within [0, tmax], or -1
+ * when it misses. */
+static double obvh_box_entry(const obvh_node* n, const double* o, const double* d, const double* inv, double tmax)
+{
+    double t0 = 0.0, t1 = tmax;
+    for (int a = 0; a < 3; a++) {
+        if (d[a] == 0.0) {
+            if (o[a] < n->lo[a] || o[a] > n->hi[a]) return -1.0;
+            continue;
+        }
+        double ta = (n->lo[a] - o[a]) * inv[a], tb = (n->hi[a] - o[a]) * inv[a];
+        if (ta > tb) { double t = ta; ta = tb; tb = t; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+        if (t0 > t1) return -1.0;
+    }
+    return t0;
+}
+
+#define OBVH_STACK 128
+
+/* Stack traversal, nearer child first; a popped node is skipped when its
+ * entry distance exceeds the best hit found since it was pushed (plus the
+ * pad). */
+static int64_t obvh_closest_hit(const obvh* b, const float* o, const float* d, float* tbest, int* fbest)
+{
+    int64_t best = -1;
+    float bt = INFINITY;
+    int bf = 0;
+    if (b->n_nodes == 0) { *tbest = bt; *fbest = bf; return best; }
+    double od[3] = {o[0], o[1], o[2]}, dd[3] = {d[0], d[1], d[2]};
+    double inv[3];
+    for (int a = 0; a < 3; a++) inv[a] = dd[a] != 0.0 ? 1.0 / dd[a] : INFINITY;
+    int64_t stack[OBVH_STACK];
+    double entry[OBVH_STACK];
+    int sp = 0;
+    if (obvh_box_entry(&b->nodes[0], od, dd, inv, INFINITY) < 0.0) { *tbest = bt; *fbest = bf; return best; }
+    stack[sp] = 0;
+    entry[sp++] = 0.0;
+    while (sp > 0) {
+        sp--;
+        const obvh_node* n = &b->nodes[stack[sp]];
+        if (entry[sp] > (double)bt + ORC_PAD) continue;
+        if (n->left < 0) {
+            for (int64_t s = n->first; s < n->first + n->count; s++) {
+                int64_t i = b->idx[s];
+                float t;
+                int f;
+                if (ray_tri_f32(o, d, b->tv0 + 3 * i, b->te1 + 3 * i, b->te2 + 3 * i, &t, &f) &&
+                    (t < bt || (t == bt && i < best))) {
+                    bt = t; bf = f; best = i;
+                }
+            }
+            continue;
+        }
+        double tmax = (double)bt + ORC_PAD;   /* +inf while nothing was hit */
+        double el = obvh_box_entry(&b->nodes[n->left], od, dd, inv, tmax);
+        double er = obvh_box_entry(&b->nodes[n->right], od, dd, inv, tmax);
+        if (sp + 2 > OBVH_STACK) abort();   /* depth is about log2(nt): never */
+        int64_t first = n->left, second = n->right;
+        double ef = el, es = er;
+        if (er >= 0.0 && (el < 0.0 || er < el)) { first = n->right; second = n->left; ef = er; es = el; }
+        if (es >= 0.0) { stack[sp] = second; entry[sp++] = es; }
+        if (ef >= 0.0) { stack[sp] = first; entry[sp++] = ef; }
+    }
+    *tbest = bt;
+    *fbest = bf;
+    return best;
+}
+
+/* orc_trace with the closest hit of every ray found through the hierarchy
+ * above (same outputs, same arithmetic). */
+EXPORT void orc_trace_bvh(const float* verts, const int32_t* tris, int64_t nt, const float* bmin,
+                          float extent, int nf, uint64_t seed, int frame, int R,
+                          const int64_t* texels, int64_t m, float* rmin, int32_t* nfront,
+                          int32_t* nback, int64_t* best_tri, int32_t* min_back)
+{
+    float* tv0 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    float* te1 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    float* te2 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    tri_edges(verts, tris, nt, tv0, te1, te2);
+    obvh b;
+    obvh_build(&b, verts, tris, nt, tv0, te1, te2);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; i++) {
+        float o[3];
+        orc_texel_centre(bmin, extent, nf, texels[i], o);
+        float r = INFINITY;
+        int32_t cf = 0, cb = 0, rb = 0;
+        int64_t bt = -1;
+        for (int ray = 0; ray < R; ray++) {
+            float d[3], t;
+            int f;
+            orc_sphere_dir(seed, (uint32_t)texels[i], (uint32_t)frame, (uint32_t)ray, d);
+            int64_t hit = obvh_closest_hit(&b, o, d, &t, &f);
+            if (hit < 0) continue;
+            if (f) cf++; else cb++;
+            if (t < r) { r = t; bt = hit; rb = !f; }
+            else if (t == r && f) rb = 0;   /* equal nearest distance: a front hit wins */
+        }
+        rmin[i] = r;
+        nfront[i] = cf;
+        nback[i] = cb;
+        if (best_tri) best_tri[i] = bt;
+        if (min_back) min_back[i] = rb;
+    }
+    obvh_free(&b);
+    free(tv0); free(te1); free(te2);
+}
+
+/* orc_cast_rays through the hierarchy. */
+EXPORT void orc_cast_rays_bvh(const float* verts, const int32_t* tris, int64_t nt, const float* orig,
+                              const float* dirs, int64_t nr, float* tout, int32_t* front, int64_t* tri)
+{
+    float* tv0 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    float* te1 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    float* te2 = (float*)malloc(sizeof(float) * 3 * (size_t)(nt > 0 ? nt : 1));
+    tri_edges(verts, tris, nt, tv0, te1, te2);
+    obvh b;
+    obvh_build(&b, verts, tris, nt, tv0, te1, te2);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nr; i++) {
+        float t;
+        int f;
+        int64_t h = obvh_closest_hit(&b, orig + 3 * i, dirs + 3 * i, &t, &f);
+        tout[i] = t;
+        front[i] = h >= 0 ? f : 0;
+        tri[i] = h;
+    }
+    obvh_free(&b);
+    free(tv0); free(te1); free(te2);
+}
+
+/* ======================================================================
  * Pin only: exact unsigned distance from points to a triangle mesh, fp64.
  * Closest point on a triangle by Voronoi-region classification (Ericson,
  * Real-Time Collision Detection, Sec. 5.1.5), brute force over triangles.

@@ -305,3 +305,104 @@ def test_nearest_sign_follows_the_closest_ray_not_the_vote():
         assert (near.f[i] < 0) == bool(want_back)
     assert np.any(near.f[below] > 0) and np.any(vote.f[below] < 0)
     assert np.any((near.f[below] > 0) & (vote.f[below] < 0))   # the two statistics differ here
+
+
+# --------------------------------------------------------------------------
+# The hierarchy path of the oracle's closest hit equals the brute-force one
+# --------------------------------------------------------------------------
+
+def _masked_sample(mesh, nc, count, seed):
+    occ = oracle.voxelize(mesh.verts, mesh.tris, BMIN, 1.0, nc)
+    seeds, _ = oracle.jfa(occ, nc)
+    c = oracle.coarse_sdf(seeds, nc, 1.0, 0.5)
+    mask, _ = oracle.mask_fill(seeds, nc, 2.0, 0.5, c)
+    tx = np.nonzero(mask)[0]
+    return np.sort(np.random.default_rng(seed).choice(tx, min(count, tx.size), replace=False))
+
+
+@pytest.mark.parametrize("scene", ["tiny", "room", "soup", "spheres"])
+def test_bvh_trace_equals_brute_force(scene):
+    # masked texels (the tracer's real origins, next to surfaces) and
+    # uniformly random ones; every output bit for bit
+    if scene == "tiny":
+        m, nc, n = S.tiny_scene(), 32, 1500
+    elif scene == "room":
+        m, nc, n = S.room_scene(1, n_objects=60, n_spheres=20), 64, 300
+    elif scene == "soup":
+        m, nc, n = S.random_soup(4, 3000), 32, 600
+    else:
+        m, nc, n = S.animated_scene(3, n_objects=30, n_lon=16, n_lat=9), 48, 600
+    nf = 2 * nc
+    tex = np.unique(np.concatenate([_masked_sample(m, nc, n, 1),
+                                    np.random.default_rng(2).choice(nf ** 3, n // 3, replace=False)]))
+    for frame in (0, 1):
+        a = oracle.trace(m.verts, m.tris, BMIN, 1.0, nf, 7, frame, 16, tex, nearest=True)
+        b = oracle.trace(m.verts, m.tris, BMIN, 1.0, nf, 7, frame, 16, tex, nearest=True, accel="bvh")
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.isfinite(a[0]).mean() > 0.5
+
+
+def test_bvh_cast_rays_grazing_and_axis_parallel():
+    # rays in the planes of axis-aligned box faces and along their edges,
+    # rays through vertices, zero direction components, origins on faces,
+    # and random near-grazing directions: the hierarchy must not skip a
+    # triangle that the fp32 test accepts
+    m = S.merge([S.box_mesh((0.5, 0.5, 0.5), 0.25), S.box_mesh((0.3, 0.7, 0.3), 0.1),
+                 S.icosphere_mesh(2, (0.7, 0.3, 0.6), 0.12)])
+    rng = np.random.default_rng(8)
+    o, d = [], []
+    for _ in range(3000):
+        axis = rng.integers(0, 3)
+        p = rng.uniform(0.2, 0.8, 3)
+        p[axis] = rng.choice([0.25, 0.75, 0.2, 0.4, 0.5])        # on a face plane
+        q = rng.normal(size=3)
+        q[axis] = rng.choice([0.0, 1e-7, -1e-7, 1e-4])            # in or next to that plane
+        o.append(p)
+        d.append(q / np.linalg.norm(q))
+    for vtx in m.verts[::7]:
+        p = rng.uniform(0, 1, 3)
+        o.append(p)
+        d.append((vtx - p) / np.linalg.norm(vtx - p))              # aimed at a vertex
+    for k in range(300):
+        q = np.zeros(3)
+        q[k % 3] = 1.0 if k % 2 else -1.0                          # two zero components
+        o.append(rng.uniform(0.1, 0.9, 3))
+        d.append(q)
+    o = np.array(o, np.float32)
+    d = np.array(d, np.float32)
+    a = oracle.cast_rays(m.verts, m.tris, o, d)
+    b = oracle.cast_rays(m.verts, m.tris, o, d, accel="bvh")
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.isfinite(a[0]).mean() > 0.3
+
+
+def test_bvh_exact_distance_ties_keep_the_smaller_index():
+    # a floor of 8 x 8 quads on a dyadic grid, each split along a diagonal,
+    # triangles in shuffled order; rays straight down onto shared edges and
+    # vertices hit several triangles at exactly the same fp32 distance, and
+    # the smaller triangle index must win whatever order the hierarchy
+    # visits them in
+    g = 8
+    verts = np.array([[i / g, 0.5, k / g] for k in range(g + 1) for i in range(g + 1)], np.float32)
+    tris = []
+    for k in range(g):
+        for i in range(g):
+            a, b, c, d = k * (g + 1) + i, k * (g + 1) + i + 1, (k + 1) * (g + 1) + i + 1, (k + 1) * (g + 1) + i
+            tris += [[a, c, b], [a, d, c]]
+    tris = np.array(tris, np.int32)[np.random.default_rng(3).permutation(2 * g * g)]
+    o, d = [], []
+    for k in range(g):
+        for i in range(g):
+            for s in (0.25, 0.5, 0.75):
+                o.append([(i + s) / g, 0.75, (k + s) / g])         # on a diagonal
+            o.append([(i + 0.5) / g, 0.75, k / g])                # on a shared grid edge
+            o.append([i / g, 0.75, k / g])                        # on a shared vertex
+    o = np.array(o, np.float32)
+    d = np.tile(np.array([[0.0, -1.0, 0.0]], np.float32), (o.shape[0], 1))
+    a = oracle.cast_rays(verts, tris, o, d)
+    b = oracle.cast_rays(verts, tris, o, d, accel="bvh")
+    assert np.all(a[0] == np.float32(0.25))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
