@@ -287,12 +287,18 @@ rtsdf_status rtsdf_shadow_backward(rtsdf_t ctx, const float* sdf, const float* p
  * all three are caller-owned device buffers of n^3 elements that must not
  * overlap.  The only scratch is a fixed 8 MiB array inside the library
  * (n <= 128; larger n returns RTSDF_E_ARG), which every GPU that loads the
- * library keeps until the process exits.  The first call on a device looks
- * up that array's address (once per device; make this first call before any
- * stream capture).  All calls share the array: two calls that overlap on the
- * GPU (e.g. on different streams) race and both results are undefined.
- * Work is enqueued on `stream` (NULL = legacy default stream); launch errors
- * return RTSDF_E_CUDA. */
+ * library keeps until the process exits.  The first call in each CUDA
+ * context (normally once per device) does a one-time set-up: it looks up
+ * that array's device address in the current context and remembers it for
+ * that context; make this first call before any stream capture starts.  A
+ * context created later (another context on the device, or the primary
+ * context again after cudaDeviceReset) gets its own lookup.  All calls share
+ * the array, which keeps the last call's contents: two calls that overlap
+ * on the GPU (e.g. on different streams) race and both results are
+ * undefined.  Work is enqueued on `stream` (NULL = legacy default stream).
+ * RTSDF_E_CUDA means the set-up or one of this call's own launches failed;
+ * the status is taken from those calls alone, so an error left pending by
+ * an unrelated earlier launch is neither returned nor cleared. */
 rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* seeds_out, float* coarse_out,
                                int32_t n, float extent, float beta_vox, void* stream);
 

@@ -14,6 +14,8 @@
 #include <math.h>
 #include <math_constants.h>
 
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -172,34 +174,79 @@ cudaError_t launch_jfa(rtsdf_ctx* c) {
 // can synchronise the device -- cannot let the library allocate.  This entry
 // point runs the same passes as rtsdf_jfa on caller buffers; its only
 // scratch (the second ping-pong grid) is the fixed array below, which every
-// GPU that loads the library holds until the process exits.
+// GPU that loads the library holds until the process exits.  Calls share the
+// array, so calls that overlap on the GPU race; every pass rewrites the part
+// of it that the next pass reads, so nothing needs clearing between calls.
 // ---------------------------------------------------------------------------
 
 namespace {
 
 constexpr int NOALLOC_MAX_N = 128;             // 128^3 x 4 B = 8 MiB of scratch
-constexpr int NOALLOC_MAX_DEVICES = 64;
+constexpr int NOALLOC_CACHE = 64;              // contexts remembered
 
 static __device__ __align__(256) uint32_t g_jfa_scratch[NOALLOC_MAX_N * NOALLOC_MAX_N * NOALLOC_MAX_N];
 
-std::mutex g_scratch_mutex;
-uint32_t* g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+// The array's device address differs between CUDA contexts (each context
+// loads its own copy of the module), so it is remembered per context, keyed
+// by the context's unique id (cuCtxGetId: never reused within a process, so
+// a context created after cudaDeviceReset gets a fresh lookup even if its
+// handle value repeats).  The two driver calls are resolved through the
+// runtime, so the library does not link libcuda itself.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
-cudaError_t scratch_for_current_device(uint32_t** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+std::mutex g_scratch_mutex;
+PfnCtxGetCurrent g_ctx_current = nullptr;
+PfnCtxGetId g_ctx_id = nullptr;
+bool g_driver_resolved = false;
+unsigned long long g_cache_id[NOALLOC_CACHE] = {};
+uint32_t* g_cache_ptr[NOALLOC_CACHE] = {};
+int g_cache_n = 0, g_cache_next = 0;
+
+void resolve_driver_calls() {
+    if (g_driver_resolved) return;
+    g_driver_resolved = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_id = reinterpret_cast<PfnCtxGetId>(f);
+}
+
+// Device address of the scratch array in the current context.  The lookup
+// (cudaGetSymbolAddress, with the caller's device and context current) runs
+// once per context; without a current context, or if the driver calls are
+// unavailable, it runs on every call (the runtime then makes the device's
+// primary context current).
+cudaError_t scratch_for_current_context(uint32_t** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_jfa_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+    resolve_driver_calls();
+    unsigned long long id = 0;
+    bool keyed = false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_current && g_ctx_id && g_ctx_current(&ctx) == CUDA_SUCCESS && ctx != nullptr &&
+        g_ctx_id(ctx, &id) == CUDA_SUCCESS)
+        keyed = true;
+    if (keyed)
+        for (int i = 0; i < g_cache_n; i++)
+            if (g_cache_id[i] == id) {
+                *out = g_cache_ptr[i];
+                return cudaSuccess;
+            }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_jfa_scratch);
+    if (e != cudaSuccess) return e;
+    if (keyed) {
+        g_cache_id[g_cache_next] = id;
+        g_cache_ptr[g_cache_next] = static_cast<uint32_t*>(p);
+        g_cache_next = (g_cache_next + 1) % NOALLOC_CACHE;
+        if (g_cache_n < NOALLOC_CACHE) g_cache_n++;
     }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<uint32_t*>(p);
     return cudaSuccess;
 }
 
@@ -229,29 +276,37 @@ extern "C" rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* se
         overlaps(seeds_out, n3 * 4, coarse_out, n3 * 4))
         return RTSDF_E_ARG;
     uint32_t* scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) return RTSDF_E_CUDA;
+    if (scratch_for_current_context(&scratch) != cudaSuccess) return RTSDF_E_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const float hc = extent / (float)n;
-    const float beta_h = beta_vox * hc;
+    float hc = extent / (float)n;
+    float beta_h = beta_vox * hc;
     int L = 0;
     while ((1 << L) < n) L++;
+    // every launch goes through cudaLaunchKernel, whose return value is the
+    // status of that launch alone (an error left pending by someone else's
+    // earlier launch is neither reported nor cleared here)
+    size_t nn = n3;
+    int ni = n;
     if (L == 0) {
-        k_copy_u32<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(seeds_in, seeds_out, n3);
-        k_coarse_only<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(seeds_in, n3, n, coarse_out, hc, beta_h);
-    } else {
-        // pass i (1-based, L passes) writes seeds_out when L - i is even, else
-        // the scratch array, so the last pass lands in seeds_out
-        dim3 block(32, 8, 1), grid((n + 31) / 32, (n + 7) / 8, n);
-        const uint32_t* in = seeds_in;
-        for (int i = 1; i <= L; i++) {
-            const int k = 1 << (L - i);
-            uint32_t* out = ((L - i) % 2 == 0) ? seeds_out : scratch;
-            if (i == L)
-                k_jfa_pass<true, 32, 8><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
-            else
-                k_jfa_pass<false, 32, 8><<<grid, block, 0, s>>>(in, out, n, k, coarse_out, hc, beta_h);
-            in = out;
-        }
+        const dim3 grid((unsigned)((n3 + 255) / 256)), block(256);
+        void* a_copy[] = {(void*)&seeds_in, (void*)&seeds_out, (void*)&nn};
+        if (cudaLaunchKernel((const void*)k_copy_u32, grid, block, a_copy, 0, s) != cudaSuccess) return RTSDF_E_CUDA;
+        void* a_coarse[] = {(void*)&seeds_in, (void*)&nn, (void*)&ni, (void*)&coarse_out, (void*)&hc, (void*)&beta_h};
+        if (cudaLaunchKernel((const void*)k_coarse_only, grid, block, a_coarse, 0, s) != cudaSuccess)
+            return RTSDF_E_CUDA;
+        return RTSDF_OK;
     }
-    return cudaGetLastError() == cudaSuccess ? RTSDF_OK : RTSDF_E_CUDA;
+    // pass i (1-based, L passes) writes seeds_out when L - i is even, else
+    // the scratch array, so the last pass lands in seeds_out
+    const dim3 block(32, 8, 1), grid((n + 31) / 32, (n + 7) / 8, n);
+    const uint32_t* in = seeds_in;
+    for (int i = 1; i <= L; i++) {
+        int k = 1 << (L - i);
+        uint32_t* out = ((L - i) % 2 == 0) ? seeds_out : scratch;
+        void* args[] = {(void*)&in, (void*)&out, (void*)&ni, (void*)&k, (void*)&coarse_out, (void*)&hc, (void*)&beta_h};
+        const void* fn = (i == L) ? (const void*)k_jfa_pass<true, 32, 8> : (const void*)k_jfa_pass<false, 32, 8>;
+        if (cudaLaunchKernel(fn, grid, block, args, 0, s) != cudaSuccess) return RTSDF_E_CUDA;
+        in = out;
+    }
+    return RTSDF_OK;
 }

@@ -42,7 +42,12 @@ def _noalloc(occ, nc, beta):
 
 
 def test_noalloc_matches_rtsdf_jfa_on_two_calls():
-    cases = [(S.room_scene(1, n_objects=40), 128, 0.5), (S.tiny_scene(), 48, 0.25)]
+    # pass counts 7 (odd, last pass reads the scratch array), 6 (even), 5,
+    # 1 (a single pass straight into seeds_out), 2, and 0 (n = 1: copy and
+    # coarse SDF only)
+    cases = [(S.room_scene(1, n_objects=40), 128, 0.5), (S.tiny_scene(), 48, 0.25),
+             (S.tiny_scene(), 32, 0.5), (S.tiny_scene(), 2, 0.5), (S.tiny_scene(), 3, 0.5),
+             (S.tiny_scene(), 1, 0.5)]
     for mesh, nc, beta in cases:
         occ, seeds, coarse = _reference(mesh, nc, beta)
         out_s, out_c = _noalloc(occ, nc, beta)
