@@ -99,6 +99,8 @@ def _load():
             "orc_shadow": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
                                   c_d, c_d, f64p, ctypes.c_void_p, ctypes.c_void_p]),
             "orc_shadow_jitter": (None, [c_u64, c_u32, c_i64, f64p]),
+            "orc_shadow_margin": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
+                                         c_d, c_d, f64p]),
             "orc_shadow_exact": (None, [f32p, i32p, c_i64, f32p, f32p, c_i64, f32p, c_f, i32p]),
             "orc_shadow_grad": (None, [f32p, c_int, f64p, c_d, f32p, f32p, c_i64, f64p, c_d, c_int,
                                        c_d, c_d, f64p, f64p, f64p]),
@@ -481,6 +483,21 @@ def shadow(sdf, n, bmin, extent, pos, nrm, light_v, k, steps, step_max, eps, inf
     if info:
         return vis, inf.reshape(-1, 3)
     return vis
+
+
+def shadow_margin(sdf, n, bmin, extent, pos, nrm, light_v, k, steps, step_max, eps):
+    """Per shading point, the smallest relative gap over its march between
+    the two sides of any discrete decision (inside the volume, h < eps,
+    t - y > 0, a new minimum of the penumbra estimate, h < step_max, the
+    root's argument > 0), fp64.  A march with a margin well above the
+    rounding of another precision takes the same discrete path there."""
+    s = _f32(sdf).reshape(-1)
+    p, q = _f32(pos).reshape(-1, 3), _f32(nrm).reshape(-1, 3)
+    out = np.empty(p.shape[0])
+    _load().orc_shadow_margin(s, n, np.asarray(bmin, np.float64), float(extent), p.reshape(-1), q.reshape(-1),
+                              p.shape[0], np.asarray(light_v, np.float64), float(k), int(steps), float(step_max),
+                              float(eps), out)
+    return out
 
 
 def unit_light(light_v):

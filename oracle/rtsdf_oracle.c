@@ -979,27 +979,62 @@ static int inside_box(const double* q, const double* bmin, double extent)
 /* Forward march of one point; records per step (t_i, h_i) when arrays given.
  * Returns visibility; *nstep = samples taken, *argmin = step that set res
  * (-1 if none), *term = 1 if stopped by h < eps. */
+/* Relative closeness of two values that a decision compares. */
+static double rel_gap(double a, double b, double scale)
+{
+    return fabs(a - b) / scale;
+}
+
 static double march_one(const float* f, const march_cfg* mc, const double* p, const double* nrm,
                         const double* L, double shift, double* ts, double* hs, int* nstep, int* argmin,
-                        int* term)
+                        int* term, double* margin)
 {
-    /* shift: the origin's jitter toward the light (Sec. 2.3), world units */
+    /* shift: the origin's jitter toward the light (Sec. 2.3), world units.
+     * margin (may be NULL): the smallest relative gap, over the whole march,
+     * between the two sides of any discrete decision (inside the volume,
+     * h < eps, t - y > 0, a new minimum, h < step_max, the root's argument
+     * > 0); a march with a large margin takes the same path under small
+     * perturbations of its inputs or rounding. */
     double o[3];
     for (int a = 0; a < 3; a++) o[a] = p[a] + 2.0 * mc->eps * nrm[a] + shift * L[a];
     double t = 0.0, res = 1.0, ph = 1e20;
+    double mg = INFINITY;
     int am = -1, i;
     *term = 0;
     for (i = 0; i < mc->steps; i++) {
         double q[3] = {o[0] + t * L[0], o[1] + t * L[1], o[2] + t * L[2]};
+        if (margin)
+            for (int a = 0; a < 3; a++) {
+                double lo = rel_gap(q[a], mc->bmin[a], mc->h), hi = rel_gap(q[a], mc->bmin[a] + mc->extent, mc->h);
+                if (lo < mg) mg = lo;
+                if (hi < mg) mg = hi;
+            }
         if (!inside_box(q, mc->bmin, mc->extent)) break;
         double h = trilinear(f, mc->n, mc->bmin, mc->h, q, NULL);
         if (ts) { ts[i] = t; hs[i] = h; }
-        if (h < mc->eps) { *term = 1; *nstep = i + 1; *argmin = am; return 0.0; }
+        if (margin) {
+            double g1 = rel_gap(h, mc->eps, mc->eps);
+            if (g1 < mg) mg = g1;
+        }
+        if (h < mc->eps) { *term = 1; *nstep = i + 1; *argmin = am; if (margin) *margin = mg; return 0.0; }
         double y = h * h / (2.0 * ph);
         double a2 = h * h - y * y;
         double dd = sqrt(a2 > 0.0 ? a2 : 0.0);
+        if (margin) {
+            /* at t = 0 (the first step) t - y > 0 is false at any precision */
+            double g2 = t > 0.0 ? rel_gap(t, y, mc->h) : INFINITY;
+            double g3 = rel_gap(a2, 0.0, h * h), g4 = rel_gap(h, mc->step_max, mc->step_max);
+            if (g2 < mg) mg = g2;
+            if (g3 < mg) mg = g3;
+            if (g4 < mg) mg = g4;
+        }
         if (t - y > 0.0) {
             double g = mc->k * dd / (t - y);
+            if (margin) {
+                double sc = fmax(fabs(g), fabs(res));
+                double g5 = sc > 0.0 ? rel_gap(g, res, sc) : 0.0;
+                if (g5 < mg) mg = g5;
+            }
             if (g < res) { res = g; am = i; }
         }
         ph = h;
@@ -1007,6 +1042,7 @@ static double march_one(const float* f, const march_cfg* mc, const double* p, co
     }
     *nstep = i;
     *argmin = am;
+    if (margin) *margin = mg;
     if (res < 0.0) res = 0.0;
     if (res > 1.0) res = 1.0;
     return res;
@@ -1034,7 +1070,7 @@ EXPORT void orc_shadow(const float* sdf, int n, const double* bmin, double exten
         double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
         double nn[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
         int ns, am, term;
-        vis[i] = march_one(sdf, &mc, p, nn, L, shift ? shift[i] : 0.0, NULL, NULL, &ns, &am, &term);
+        vis[i] = march_one(sdf, &mc, p, nn, L, shift ? shift[i] : 0.0, NULL, NULL, &ns, &am, &term, NULL);
         if (info) { info[3 * i] = ns; info[3 * i + 1] = am; info[3 * i + 2] = term; }
     }
 }
@@ -1092,6 +1128,26 @@ EXPORT void orc_shadow_jitter(uint64_t seed, uint32_t frame, int64_t npix, doubl
  * Zero derivative where the march stopped on h < eps, where no step set
  * res (res = 1), or where dd was clamped to 0.  L = v/|v|.
  * ====================================================================== */
+/* Per shading point, the march's decision margin (see march_one): points
+ * whose margin is small may take another discrete path (another step
+ * count, another minimising step, termination) when the march is
+ * evaluated at another precision. */
+EXPORT void orc_shadow_margin(const float* sdf, int n, const double* bmin, double extent,
+                              const float* pos, const float* nrm, int64_t npix, const double* light_v,
+                              double k, int steps, double step_max, double eps, double* margin)
+{
+    march_cfg mc = {n, extent / n, extent, eps, k, step_max, steps, bmin};
+    double L[3];
+    normalise3(light_v, L);
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < npix; i++) {
+        double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+        double nn[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+        int ns, am, term;
+        march_one(sdf, &mc, p, nn, L, 0.0, NULL, NULL, &ns, &am, &term, &margin[i]);
+    }
+}
+
 EXPORT void orc_shadow_grad(const float* sdf, int n, const double* bmin, double extent,
                             const float* pos, const float* nrm, int64_t npix, const double* light_v,
                             double k, int steps, double step_max, double eps, const double* dvis,
@@ -1112,7 +1168,7 @@ EXPORT void orc_shadow_grad(const float* sdf, int n, const double* bmin, double 
             double p[3] = {pos[3 * pi], pos[3 * pi + 1], pos[3 * pi + 2]};
             double nn[3] = {nrm[3 * pi], nrm[3 * pi + 1], nrm[3 * pi + 2]};
             int ns, am, term;
-            march_one(sdf, &mc, p, nn, L, 0.0, ts, hs, &ns, &am, &term);
+            march_one(sdf, &mc, p, nn, L, 0.0, ts, hs, &ns, &am, &term, NULL);
             if (term || am < 0) continue;
             double o[3];
             for (int a = 0; a < 3; a++) o[a] = p[a] + 2.0 * eps * nn[a];

@@ -85,9 +85,21 @@ def test_eq1_decay(alpha):
     assert np.max(np.abs(u[m_] - pipe.u[m_])) <= 1e-6
 
 
+def _oracle_masked_texels(mesh, nc, beta, d):
+    """Fine texels that the oracle's own Sec. 2.1 pipeline and Eq. 1 mask
+    select (the samples below come from the oracle, not from the GPU)."""
+    occ = oracle.voxelize(mesh.verts, mesh.tris, BMIN, 1.0, nc)
+    seeds, _ = oracle.jfa(occ, nc)
+    c = oracle.coarse_sdf(seeds, nc, 1.0, beta)
+    mask, _ = oracle.mask_fill(seeds, nc, d, beta, c)
+    return np.nonzero(mask)[0]
+
+
 def test_room_sampled_texels():
     # procedural room (~100k triangles) at 128^3 -> 256^3, 64 rays, 2 frames;
-    # the oracle traces a seeded sample of the masked texels by brute force
+    # 200,000 of the oracle's masked texels are traced by the oracle (its
+    # hierarchy path, bit-identical to brute force).  With no mismatch in
+    # 200,000 texels the grazing-hit rate is below 1.5e-5 at 95 % confidence.
     from paper_2210_04449_gb300 import RTSDF
     m = S.room_scene(1)
     nc, d, beta, R = 128, 2.0, 0.5, 64
@@ -97,14 +109,39 @@ def test_room_sampled_texels():
     for t in range(2):
         rt.update(d, R, t)
     rt.sync()
-    n_m = rt.masked_count()
-    masked = rt.grids()["masked"].cpu().numpy()[:n_m]
-    tex = child_texels(masked, nc)
-    sample = np.sort(np.random.default_rng(11).choice(tex, 96, replace=False))
-    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 1, track=sample)
+    tex = _oracle_masked_texels(m, nc, beta, d)
+    sample = np.sort(np.random.default_rng(11).choice(tex, 200_000, replace=False))
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 1, track=sample, accel="bvh")
     for t in range(2):
         pipe.frame(m.verts, m.tris, t, R)
     _compare(rt, pipe, sample, "room sample")
+
+
+_FULL = {}
+
+
+def _full_size_oracle():
+    """The oracle's two frames of the benchmark workload on 50,000 texels
+    sampled from its own frame-0 mask (computed once for both builders),
+    plus its frame-1 mask and fill."""
+    if _FULL:
+        return _FULL
+    mesh = S.animated_scene(2, n_objects=500)
+    nc, d, beta, R, seed = 256, 2.0, 0.5, 64, 2
+    tex = _oracle_masked_texels(mesh, nc, beta, d)
+    sample = np.sort(np.random.default_rng(12).choice(tex, 50_000, replace=False))
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, seed, track=sample, accel="bvh")
+    pipe.frame(mesh.verts, mesh.tris, 0, R)
+    tr = S.object_translations(seed, 1, mesh.n_objects, 0.5 / nc)
+    lo = np.stack([mesh.verts[mesh.vert_object == k].min(0) for k in range(mesh.n_objects)])
+    hi = np.stack([mesh.verts[mesh.vert_object == k].max(0) for k in range(mesh.n_objects)])
+    mv = np.any(tr != 0, axis=1)
+    verts1 = (mesh.verts + tr[mesh.vert_object]).astype(np.float32)
+    out = pipe.frame(verts1, mesh.tris, 1, R, moved_aabbs=(lo[mv], hi[mv]))
+    _, fill = oracle.mask_fill(out["seeds"], nc, d, beta, out["c"])
+    _FULL.update(mesh=mesh, tr=tr, sample=sample, pipe=pipe, mask=out["mask"], fill=fill,
+                 nc=nc, d=d, beta=beta, R=R, seed=seed)
+    return _FULL
 
 
 @pytest.mark.parametrize("builder,refit", [("sah", False), ("two_level", True)])
@@ -112,12 +149,13 @@ def test_full_size_animated_frames_sampled_texels(builder, refit):
     # the benchmark workload: 500 displaced spheres (1,000,000 triangles),
     # 256^3 -> 512^3, 64 rays per texel, every object moved before the second
     # frame (BVH rebuild -- or the two-level refit --, re-voxelize, JFA,
-    # reset), in the autotuned launch configuration the benchmark times; 96
-    # fine texels sampled from the masked ones are traced by the oracle by
-    # brute force over all triangles
+    # reset), in the autotuned launch configuration the benchmark times;
+    # 50,000 fine texels sampled from the oracle's own mask are traced by the
+    # oracle (hierarchy path).  The second frame's whole mask set and the
+    # fill of every unmasked texel (134M texels) are compared too.
     from paper_2210_04449_gb300 import RTSDF
-    mesh = S.animated_scene(2, n_objects=500)
-    nc, d, beta, R, seed = 256, 2.0, 0.5, 64, 2
+    o = _full_size_oracle()
+    mesh, nc, d, beta, R, seed = o["mesh"], o["nc"], o["d"], o["beta"], o["R"], o["seed"]
     rt = RTSDF(nc, beta_vox=beta, seed=seed)
     rt.set_bvh_builder(builder)
     rt.upload_mesh(mesh.verts, mesh.tris)
@@ -125,23 +163,25 @@ def test_full_size_animated_frames_sampled_texels(builder, refit):
     rt.build_bvh()
     rt.update(d, R, 0)
     rt.autotune(d, R, 1, use_cache=True)          # saves and restores the state
-    n_m = rt.masked_count()
-    masked = rt.grids()["masked"].cpu().numpy()[:n_m]
-    sample = np.sort(np.random.default_rng(12).choice(child_texels(masked, nc), 96, replace=False))
-    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, seed, track=sample)
-    pipe.frame(mesh.verts, mesh.tris, 0, R)
-    tr = S.object_translations(seed, 1, mesh.n_objects, 0.5 / nc)
-    lo = np.stack([mesh.verts[mesh.vert_object == k].min(0) for k in range(mesh.n_objects)])
-    hi = np.stack([mesh.verts[mesh.vert_object == k].max(0) for k in range(mesh.n_objects)])
-    mv = np.any(tr != 0, axis=1)
-    verts1 = (mesh.verts + tr[mesh.vert_object]).astype(np.float32)
-    rt.move_objects(tr)
+    rt.move_objects(o["tr"])
     rt.build_bvh(refit=refit)
     rt.update(d, R, 1)
-    pipe.frame(verts1, mesh.tris, 1, R, moved_aabbs=(lo[mv], hi[mv]))
     rt.sync()
-    exact = _compare(rt, pipe, sample, f"animated 1M full size sample ({builder}, refit={refit})")
+    exact = _compare(rt, o["pipe"], o["sample"], f"animated 1M full size sample ({builder}, refit={refit})")
     assert exact == 1.0
+    g = rt.grids()
+    n_m = rt.masked_count()
+    masked_g = np.sort(g["masked"].cpu().numpy()[:n_m].astype(np.int64))
+    masked_o = np.unique(oracle.parent_index(nc)[o["mask"]])
+    assert np.array_equal(masked_g, masked_o)
+    f = g["fine"].cpu().numpy()
+    um = ~o["mask"]
+    fu, fo = f[um].astype(np.float64), o["fill"][um]
+    fin = np.isfinite(fo)
+    assert np.array_equal(fin, np.isfinite(fu))
+    assert np.max(np.abs(fu[fin] - fo[fin])) <= 1e-6
+    print(f"full size mask: {masked_o.size} coarse voxels, {int(o['mask'].sum())} texels, fill of "
+          f"{int(um.sum())} texels within 1e-6")
 
 
 def test_motion_refit_and_reset():

@@ -297,3 +297,29 @@ def test_fallback_takes_the_umbra_only_where_blocked():
     vis = np.array([0.0, 0.3, 1.0, 0.7])
     blocked = np.array([True, True, False, False])
     np.testing.assert_array_equal(oracle.shadow_fallback(vis, blocked), [0.0, 0.0, 1.0, 0.7])
+
+
+def test_decision_margin_predicts_a_stable_march_path():
+    # A point whose march keeps every discrete decision at a relative gap
+    # above 1e-2 must take the same path (step count, minimising step,
+    # termination) when the grid is perturbed by 1e-4 relative noise; the
+    # noise must change the path of some points, and only of points with a
+    # small margin.
+    nf = 64
+    g = np.minimum(S.sphere_grid_sdf(nf, (0.5, 0.35, 0.5), 0.12), S.box_grid_sdf(nf, (0.3, 0.3, 0.65), 0.06))
+    c = (np.arange(nf) + 0.5) / nf
+    grid = np.minimum(g, (c[None, :, None] - 0.1) * np.ones((nf, nf, nf))).astype(np.float32)
+    pos, nrm = S.floor_gbuffer(256, 256, y=0.1, lo=0.05, hi=0.95)
+    L, h = (0.4, 1.0, 0.3), 1.0 / nf
+    cfg = (8.0, 64, 4 * h, h)
+    m = oracle.shadow_margin(grid, nf, BMIN, 1.0, pos, nrm, L, *cfg)
+    _, i0 = oracle.shadow(grid, nf, BMIN, 1.0, pos, nrm, L, *cfg, info=True)
+    rng = np.random.default_rng(4)
+    changed = np.zeros(m.size, bool)
+    for _ in range(4):
+        noisy = (grid.astype(np.float64) * (1 + rng.normal(0, 1e-4, grid.shape))).astype(np.float32)
+        _, i1 = oracle.shadow(noisy, nf, BMIN, 1.0, pos, nrm, L, *cfg, info=True)
+        changed |= np.any(i0 != i1, axis=1)
+    assert changed.sum() >= 5
+    assert np.all(m[changed] <= 1e-2)
+    assert 0.9 < np.mean(m > 1e-2) < 1.0
