@@ -6,11 +6,13 @@
 // (= smaller linear index).  Steps are 2^(ceil(log2 N) - 1), ..., 2, 1.
 // The last pass also writes the coarse SDF c = h_c sqrt(D2) - beta h_c.
 //
-// Seeds are packed bytes (x, y, z, 0), so D2 needs two byte dot products:
-//   D2 = s.s - 2 s.v + v.v   (dp4a; wraps correctly modulo 2^32, D2 < 2^18)
-// and "no seed" (all ones) is pushed above every real distance by OR-ing
-// the seed's top byte into D2.  The candidate key is then the pair
-// (D2, seed), compared lexicographically.
+// Seeds are packed bytes (x, y, z, 0).  The one-voxel-per-thread passes
+// (jfa_dev.cuh) compute D2 with two byte dot products,
+//   D2 = s.s - 2 s.v + v.v   (dp4a; wraps correctly modulo 2^32, D2 < 2^18),
+// and push "no seed" (all ones) above every real distance by OR-ing the
+// seed's top byte into D2; the z-blocked pass below shares the x/y part of
+// D2 between the voxels of a column.  Either way the candidate key is the
+// pair (D2, seed), compared lexicographically.
 #include <math.h>
 #include <math_constants.h>
 
@@ -50,12 +52,31 @@ void launch_pass(rtsdf_ctx* c, const uint32_t* in, uint32_t* out, int n, int k, 
 }
 
 // z-blocked pass: a thread floods T voxels of one z-lattice column,
-// (x, y, rz + k (T g + t)) for t < T, so the T + 2 candidate z-slices are
-// loaded once and shared (9 (T + 2) loads for 27 T candidates).  Blocks are
-// 32 x 4 threads in (x, y); blockIdx.z = g k + rz.  An x or y offset that
-// leaves the grid reads the voxel's own coordinate on that axis (a duplicate
-// of another candidate), a z-slice outside the grid holds no seed; both
-// leave the arg-min over the voxels inside the grid unchanged.
+// (x, y, z_t = rz + k (T g + t)) for t < T; blocks are 32 x 4 threads in
+// (x, y), blockIdx.z = g k + rz.  The T + 2 candidate z-slices (9 voxels
+// each) are read once and shared by the column's voxels.
+//
+// Per candidate seed s = (sx, sy, sz, 0) of a slice, once:
+//   A = (sx - x)^2 + (sy - y)^2 + sz^2            vabsdiff4 + dp4a
+//       OR-ed with s's top byte (as 0x7F000000):  a seedless candidate
+//       (all ones) lands above every real key
+// Per voxel z_t and candidate, one instruction:
+//   key = A - 2 z_t sz = D2 - z_t^2               dp2a.hi (16-bit -2 z_t times byte 2)
+// Keys of one voxel share the z_t^2 offset, so their order is D2's; the
+// arg-min is the smallest key (three-input signed minima), then the smallest
+// seed among the candidates at that key -- the lexicographic (D2, seed)
+// minimum.  An x or y offset that leaves the grid reads the voxel's own
+// coordinate on that axis (a duplicate of another candidate); a z-slice
+// outside the grid holds no seed.  Slices roll through registers: voxel t
+// needs slices t .. t + 2 only.
+__device__ __forceinline__ int dp2a_hi_s_u(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp2a.hi.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ int vimin3_s(int a, int b, int c) { return __vimin3_s32(a, b, c); }
+
 template <bool FINAL, int T>
 __global__ void __launch_bounds__(128, 4) k_jfa_zblock(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                                       int n, int k, float* __restrict__ coarse, float hc,
@@ -72,45 +93,58 @@ __global__ void __launch_bounds__(128, 4) k_jfa_zblock(const uint32_t* __restric
         xs[i] = (uint32_t)((x + o >= 0 && x + o < n) ? x + o : x);
         ys[i] = (uint32_t)((y + o >= 0 && y + o < n) ? y + o : y) * (uint32_t)n;
     }
-    // slice j holds z-lattice index T g + j - 1
-    uint32_t sd[T + 2][9];
-#pragma unroll
-    for (int j = 0; j < T + 2; j++) {
+    const uint32_t vxy = (uint32_t)x | ((uint32_t)y << 8);
+    // slice j (0 .. T + 1) holds z-lattice index T g + j - 1
+    uint32_t ss[T + 2][9];
+    int aa[T + 2][9];
+    auto load_slice = [&](int j) {
         const int z = rz + k * (T * g + j - 1);
         if (z >= 0 && z < n) {
             const uint32_t zo = (uint32_t)z * n2;
 #pragma unroll
             for (int iy = 0; iy < 3; iy++)
 #pragma unroll
-                for (int ix = 0; ix < 3; ix++) sd[j][3 * iy + ix] = __ldg(in + zo + ys[iy] + xs[ix]);
+                for (int ix = 0; ix < 3; ix++) {
+                    const uint32_t sv = __ldg(in + zo + ys[iy] + xs[ix]);
+                    const uint32_t d = __vabsdiffu4(sv, vxy);
+                    ss[j][3 * iy + ix] = sv;
+                    aa[j][3 * iy + ix] = (int)(__dp4a(d, d, 0u) | ((sv >> 1) & 0x7F000000u));
+                }
         } else {
 #pragma unroll
-            for (int c = 0; c < 9; c++) sd[j][c] = SEED_EMPTY;
+            for (int c = 0; c < 9; c++) {
+                ss[j][c] = SEED_EMPTY;
+                aa[j][c] = 0x7F000000;
+            }
         }
-    }
+    };
+    load_slice(0);
+    load_slice(1);
 #pragma unroll
     for (int t = 0; t < T; t++) {
+        load_slice(t + 2);
         const int z = rz + k * (T * g + t);
         if (z >= n) break;
-        const uint32_t v = pack_seed(x, y, z);
-        const uint32_t vv = __dp4a(v, v, 0u);
-        uint32_t cd[27];
+        // 16-bit -2 z in the low half, 0 in the high half (byte 3 is 0 or, for
+        // a seedless candidate, already pushed out of range through A)
+        const uint32_t wz = (uint32_t)(-2 * z) & 0xFFFFu;
+        int key[27];
 #pragma unroll
         for (int j = 0; j < 3; j++)
 #pragma unroll
-            for (int c = 0; c < 9; c++) cd[9 * j + c] = dev::seed_d2(sd[t + j][c], v, vv);
-        uint32_t dmin = __vimin3_u32(cd[0], cd[1], cd[2]);
+            for (int c = 0; c < 9; c++) key[9 * j + c] = dp2a_hi_s_u(wz, ss[t + j][c], aa[t + j][c]);
+        int kmin = vimin3_s(key[0], key[1], key[2]);
 #pragma unroll
-        for (int c = 3; c < 27; c += 2) dmin = __vimin3_u32(dmin, cd[c], cd[c + 1]);
+        for (int c = 3; c < 27; c += 2) kmin = vimin3_s(kmin, key[c], key[c + 1]);
         uint32_t best = SEED_EMPTY;
 #pragma unroll
         for (int j = 0; j < 3; j++)
 #pragma unroll
             for (int c = 0; c < 9; c++)
-                if (cd[9 * j + c] == dmin) best = min(best, sd[t + j][c]);
+                if (key[9 * j + c] == kmin) best = min(best, ss[t + j][c]);
         const uint32_t idx = (uint32_t)x + ys[1] + (uint32_t)z * n2;
         out[idx] = best;
-        if (FINAL) coarse[idx] = dev::coarse_value(best, dmin, hc, beta_h);
+        if (FINAL) coarse[idx] = dev::coarse_value(best, (uint32_t)(kmin + z * z), hc, beta_h);
     }
 }
 
@@ -149,10 +183,13 @@ cudaError_t launch_jfa(rtsdf_ctx* c) {
             case 1: launch_pass<64, 4>(c, in, out, n, k, k == 1, beta_h); break;
             case 2: launch_pass<128, 2>(c, in, out, n, k, k == 1, beta_h); break;
             case 3: launch_pass<32, 4>(c, in, out, n, k, k == 1, beta_h); break;
-            case 4:
-                if ((n + k - 1) / k <= 2) launch_zblock<2>(c, in, out, n, k, k == 1, beta_h);
-                else launch_zblock<4>(c, in, out, n, k, k == 1, beta_h);
+            case 4: {
+                const int lat = (n + k - 1) / k;
+                if (lat <= 2) launch_zblock<2>(c, in, out, n, k, k == 1, beta_h);
+                else if (lat <= 4) launch_zblock<4>(c, in, out, n, k, k == 1, beta_h);
+                else launch_zblock<8>(c, in, out, n, k, k == 1, beta_h);
                 break;
+            }
             default: launch_pass<32, 8>(c, in, out, n, k, k == 1, beta_h); break;
         }
         c->cur ^= 1;
