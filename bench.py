@@ -37,13 +37,17 @@ UNIT = "ms/frame"
 NC, D_VOX, BETA, RAYS, SEED = 256, 2.0, 0.5, 64, 2
 N_OBJ = 500
 
-# fp32 pipe operations per BVH node entered / per ray-triangle test in the
-# tracer's source (fma counted as 2 flops): a 4-wide node is four slab tests
-# of 6 fma + 12 min/max + 1 compare and a 5-exchange sort; Moller-Trumbore:
-# 3 crosses (3 fma + 3 mul each), 4 dots (2 fma + 1 mul), 3 subtracts,
-# 1 divide (counted as 1), 3 scales, 1 add and 5 compares.
-FLOP_PER_VISIT = 4 * (6 * 2 + 12 + 1) + 5
-FLOP_PER_TEST = 3 * (3 * 2 + 3) + 4 * (2 * 2 + 1) + 3 + 1 + 3 + 1 + 5
+# Algorithmic fp32 work of the tracer as the scope table counts it: 24 flop
+# per internal node visited (two slab tests, 6 fma each, counted as 2 flops)
+# and 30 per ray-triangle test.
+FLOP_PER_VISIT = 24
+FLOP_PER_TEST = 30
+
+# Warp instructions per traced ray of k_trace on the benchmark workload, from
+# an ncu capture of smsp__inst_executed.sum on one full-size launch (1 pass),
+# keyed like TRAFFIC below; the tracer's issue-roof fraction is computed from
+# it (null once the sources change).
+INST_PER_RAY = {}
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
 # by the sha256 of the sources it was measured on (the kernel and the BVH
@@ -92,6 +96,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--no-variant", action="store_true", help="skip the nearest-face sign variant comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the room (128^3 -> 256^3, 8 frames) and differentiable-shadow (512^3) lines")
     ap.add_argument("--bvh", default="rebuild", choices=["rebuild", "refit"],
                     help="per-frame BVH maintenance: full rebuild (default) or refit of the first frame's tree")
     ap.add_argument("--builder", default="sah", choices=["sah", "lbvh", "two_level"],
@@ -274,6 +280,27 @@ def run_gpu(args, rank, world):
     trace_tflops = rays_frame * flop_per_ray / (trace_ms * 1e-3) / 1e12 if trace_ms else None
     th = _src_hash(*TRAFFIC_SOURCES)
     traffic = TRAFFIC.get(th)
+    # the roof that binds the tracer: instruction issue, 4 schedulers per SM
+    issue_peak = sms * 4 * sm_mhz * 1e6 / 1e9          # G warp instructions / s
+    ipr = INST_PER_RAY.get(th) if nc == NC and args.objects == N_OBJ else None
+    issue = None
+    if ipr and trace_ms:
+        ach = ipr * rays_frame / (trace_ms * 1e-3) / 1e9
+        issue = {"bound": "issue", "achieved": round(ach, 1), "peak": round(issue_peak, 1),
+                 "unit": "G warp-instructions/s", "frac": round(ach / issue_peak, 4),
+                 "inst_per_ray": ipr,
+                 "source": "ncu smsp__inst_executed.sum of one full-size k_trace launch / its rays, "
+                           f"x rays / trace ms; peak {sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz"}
+
+    # mask + fill + reset: the scope table's bytes are the fine write and the
+    # coarse seed read (the reset test and the accumulator reads of masked
+    # texels come on top)
+    mask_ms = stage["mask"]
+    mask_bytes = (2 * nc) ** 3 * 4 + nc ** 3 * 4
+    mask_gbs = mask_bytes / (mask_ms * 1e-3) / 1e9 if mask_ms else None
+    mask_line = {"ms": round(mask_ms, 4) if mask_ms else None, "algorithmic_bytes": mask_bytes,
+                 "gbs": round(mask_gbs, 1) if mask_gbs else None, "peak_gbs": hbm_peak,
+                 "frac": round(mask_gbs / hbm_peak, 4) if mask_gbs else None, "peak_source": hbm_src}
 
     line = {
         "metric": METRIC,
@@ -300,6 +327,7 @@ def run_gpu(args, rank, world):
                 "algorithmic_bytes": jfa_bytes, "gbs": round(jfa_gbs, 1) if jfa_gbs else None,
                 "peak_gbs": hbm_peak, "frac": round(jfa_gbs / hbm_peak, 4) if jfa_gbs else None,
                 "peak_source": hbm_src},
+        "mask": mask_line,
         "tracer": {"node_visits_per_ray": round(visits_per_ray, 2), "tri_tests_per_ray": round(tests_per_ray, 2),
                    "flop_per_ray": round(flop_per_ray, 1),
                    # SIMT use of the traversal loop: lanes entering an internal
@@ -313,7 +341,9 @@ def run_gpu(args, rank, world):
                      "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
                      "frac": round(trace_tflops / fp32_peak_tflops, 4) if trace_tflops else None,
                      "traffic": traffic,
-                     "peak_source": f"derived: {sms} SMs x 128 fp32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"},
+                     "count": f"{FLOP_PER_VISIT} flop per internal node visit, {FLOP_PER_TEST} per triangle test",
+                     "peak_source": f"derived: {sms} SMs x 128 fp32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
+                     "issue": issue},
         "clocks": clk,
         "e2e": {"value": round(job_ms_per_frame(e2e_ms, world), 3), "unit": UNIT, "h2d_bytes_per_step": N_OBJ * 3 * 4,
                 "d2h_bytes_per_step": 8 + 4},
@@ -426,10 +456,125 @@ def run_sign_variant(dev, frames=8, rays=RAYS, nc=128):
     return out
 
 
-def run_batched(dev, frames=3, rays=32, d_vox=2.0):
+def _events_ms(fn, reps, dev):
+    """Mean ms of fn() over reps calls, CUDA events on the current stream."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def run_config2(dev, frames=8, warm=3, rays=RAYS, nc=128):
+    """The procedural room (~100k triangles) at 128^3 -> 256^3, 64 rays per
+    texel, 8 frames of the plain pipeline (voxelize, JFA, mask, trace with
+    Eq. 1); ms/frame over the frames after the first `warm`, then the soft
+    shadow pass at 1920x1080 (k = 8, 64 steps) on the frame's fine SDF."""
+    import numpy as np
+    import torch
+
+    from paper_2210_04449_gb300 import RTSDF
+    from synth import scenes as S
+    mesh = S.room_scene(1)
+    rt = RTSDF(nc, beta_vox=BETA, seed=1)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.build_bvh()
+    rt.set_profiling(True)
+    per, trace = [], []
+    for f in range(frames):
+        rt.stats()
+        ms = _events_ms(lambda: rt.update(D_VOX, rays, f), 1, dev)
+        st = rt.stats()
+        if f >= warm:
+            per.append(ms)
+            trace.append(st["stage_ms"]["trace"])
+    m_tex = rt.masked_count() * 8
+    pos, nrm = S.floor_gbuffer(1920, 1080, y=0.02)
+    pt, nt = torch.tensor(pos, device=dev), torch.tensor(nrm, device=dev)
+    vis = torch.empty((1080, 1920), device=dev)
+    L = (0.4, 1.0, 0.3)
+    rt.shadow(pt, nt, L, k=8.0, steps=64, out=vis)
+    sh = _events_ms(lambda: rt.shadow(pt, nt, L, k=8.0, steps=64, out=vis), 5, dev)
+    rt.sync()
+    rt.close()
+    tr = float(np.mean(trace))
+    return {"workload": f"static room {nc}^3->{2 * nc}^3, {mesh.nt:,} tris, {rays} rays/texel, {frames} frames "
+                        f"(frames {warm}..{frames - 1} timed), shadow 1920x1080 k=8 64 steps",
+            "ms_per_frame": round(float(np.median(per)), 3), "trace_ms": round(tr, 3),
+            "masked_texels": int(m_tex), "rays_per_s": round(m_tex * rays / (tr * 1e-3)),
+            "shadow_1080p_ms": round(sh, 4)}
+
+
+def run_config5(dev, reps=5, warm=3, rays=RAYS, nc=256, frames=2):
+    """The differentiable shadow: the room's geometry traced at 256^3 ->
+    512^3 (64 rays, 2 frames), 1024x1024 floor points, 64 steps, k = 8;
+    loss = mean (vis - target)^2 against the target rendered with the light
+    rotated 5 degrees about the horizontal axis perpendicular to it.  One
+    step = forward march, loss and its gradient dLoss/dvis, zeroing of
+    dLoss/dsdf, and the adjoint (dLoss/dsdf, dLoss/dlight)."""
+    import numpy as np
+    import torch
+
+    from paper_2210_04449_gb300 import RTSDF
+    from synth import scenes as S
+    mesh = S.room_scene(1)
+    rt = RTSDF(nc, beta_vox=BETA, seed=1)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.build_bvh()
+    for f in range(frames):
+        rt.update(D_VOX, rays, f)
+    L0 = np.array([0.4, 1.0, 0.3]) / np.linalg.norm([0.4, 1.0, 0.3])
+    ax = np.array([L0[2], 0.0, -L0[0]]) / np.hypot(L0[2], L0[0])
+    a = math.radians(5.0)
+    L1 = L0 * math.cos(a) + np.cross(ax, L0) * math.sin(a) + ax * np.dot(ax, L0) * (1 - math.cos(a))
+    pos, nrm = S.floor_gbuffer(1024, 1024, y=0.02)
+    pt, nt = torch.tensor(pos, device=dev), torch.tensor(nrm, device=dev)
+    target = rt.shadow(pt, nt, L1, k=8.0, steps=64)
+    vis = torch.empty_like(target)
+    dsdf = torch.zeros((2 * nc) ** 3, device=dev)
+    dl = torch.zeros(3, device=dev)
+    loss = torch.zeros((), device=dev)
+    inv = 1.0 / target.numel()
+
+    def fwd():
+        rt.shadow(pt, nt, L0, k=8.0, steps=64, out=vis)
+
+    def bwd():
+        dsdf.zero_()
+        dl.zero_()
+        rt.shadow_backward(pt, nt, L0, dvis, dsdf, dl, k=8.0, steps=64)
+
+    def step():
+        fwd()
+        diff = vis - target
+        loss.copy_((diff * diff).sum() * inv)
+        dvis.copy_(diff * (2.0 * inv))
+        bwd()
+    dvis = torch.empty_like(target)
+    for _ in range(warm):
+        step()
+    ms = _events_ms(step, reps, dev)
+    f_ms = _events_ms(fwd, reps, dev)
+    b_ms = _events_ms(bwd, reps, dev)
+    out = {"workload": f"room {nc}^3->{2 * nc}^3 ({mesh.nt:,} tris, {rays} rays, {frames} frames), 1024x1024 "
+                       "floor points, k=8, 64 steps, MSE vs the light rotated 5 deg",
+           "ms_per_step": round(ms, 4), "forward_ms": round(f_ms, 4), "backward_ms": round(b_ms, 4),
+           "loss": float(loss.item()), "dlight": [round(float(x), 6) for x in dl.cpu()]}
+    rt.sync()
+    rt.close()
+    return out
+
+
+def run_batched(dev, frames=8, rays=32, d_vox=2.0):
     """The batched form against plain per-scene frames on 64 uneven scenes
-    (coarse 32..128, 1k-200k triangles): ms/frame for all scenes, and whether
-    the two give identical fine grids."""
+    (coarse 32..128, 1k-200k triangles), 8 frames each after a first
+    untimed one: ms/frame for all scenes, and whether the two give the same
+    grids element by element (accumulator, counts, fine SDF)."""
     import numpy as np
     import torch
 
@@ -465,7 +610,8 @@ def run_batched(dev, frames=3, rays=32, d_vox=2.0):
     for rt in ctxs:
         for k, v in rt.stats()["stage_ms"].items():
             plain_stage[k] = plain_stage.get(k, 0.0) + v / frames
-    ref = [float(rt.grids()["fine"].double().sum().item()) for rt in ctxs]
+    # bit patterns (int32 views) of each scene's grids, kept on the device
+    ref = [{k: rt.grids()[k].view(torch.int32).clone() for k in ("accum", "counts", "fine")} for rt in ctxs]
     for rt in ctxs:
         rt.close()
     del ctxs
@@ -486,13 +632,15 @@ def run_batched(dev, frames=3, rays=32, d_vox=2.0):
         ms.append(b.stats()["last_frame_ms"])
     wall = (time.perf_counter() - t0) * 1e3 / frames
     info = b.stats()
-    got = [float(sc.grids()["fine"].double().sum().item()) for sc in b.scenes]
+    identical = all(torch.equal(sc.grids()[k].view(torch.int32), r[k]) for sc, r in zip(b.scenes, ref) for k in r)
     b.close()
+    del ref
     tris = sum(m.nt for m in meshes)
     return {"workload": f"64 scenes, coarse 32..128, {tris:,} tris total, {rays} rays/texel",
             "plain_ms_per_frame": round(plain_ms, 3), "batched_ms_per_frame": round(float(np.mean(ms)), 3),
             "batched_wall_ms_per_frame": round(wall, 3), "speedup": round(plain_ms / float(np.mean(ms)), 3),
-            "identical": bool(np.array_equal(np.array(ref), np.array(got))), "graph": bool(info["graph"]),
+            "frames": frames, "identical": bool(identical), "compared": "accum, counts, fine: every element",
+            "graph": bool(info["graph"]),
             "grid": info["grid"], "tuning": tuned, "launches_per_frame": 1, "stage_ms": info["stage_ms"],
             "plain_stage_ms": {k: round(v, 3) for k, v in plain_stage.items() if v > 0}}
 
@@ -591,6 +739,11 @@ def main():
     if not args.no_variant:
         import torch
         line["sign_variant"] = run_sign_variant(torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+    if not args.no_configs:
+        import torch
+        d = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        line["config2"] = run_config2(d)
+        line["config5"] = run_config5(d)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             # ~10 s of host work: the full coarse stages and 512 traced texels
