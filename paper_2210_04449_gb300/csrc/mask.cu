@@ -68,56 +68,77 @@ __device__ __forceinline__ void box_cells(const BinArgs& a, const float* b, int 
     }
 }
 
-__global__ void k_bin_count(BinArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *a.n_moved) return;
-    int lo[3], hi[3];
-    box_cells(a, a.boxes + 6 * a.moved[i], lo, hi);
-    for (int z = lo[2]; z <= hi[2]; z++)
-        for (int y = lo[1]; y <= hi[1]; y++)
-            for (int x = lo[0]; x <= hi[0]; x++) atomicAdd(a.count + x + a.g * (y + a.g * z), 1u);
+// One warp per moved object; its lanes share the object's range of cells.
+__device__ __forceinline__ int box_cell_range(const BinArgs& a, const float* b, int lo[3], int n[3]) {
+    int hi[3];
+    box_cells(a, b, lo, hi);
+    for (int k = 0; k < 3; k++) n[k] = hi[k] >= lo[k] ? hi[k] - lo[k] + 1 : 0;
+    return n[0] * n[1] * n[2];
 }
 
-// exclusive scan of the cell counts (one block); start[g^3] = total
+__global__ void k_bin_count(BinArgs a) {
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = (int)(threadIdx.x & 31);
+    if (w >= *a.n_moved) return;
+    int lo[3], n[3];
+    const int total = box_cell_range(a, a.boxes + 6 * a.moved[w], lo, n);
+    for (int i = lane; i < total; i += 32) {
+        const int x = lo[0] + i % n[0], y = lo[1] + (i / n[0]) % n[1], z = lo[2] + i / (n[0] * n[1]);
+        atomicAdd(a.count + x + a.g * (y + a.g * z), 1u);
+    }
+}
+
+// exclusive scan of the cell counts (one block, 1024 cells per round,
+// coalesced); start[g^3] = total
 __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
-    __shared__ uint32_t part[1024];
+    __shared__ uint32_t wsum[32];
     const int64_t total = (int64_t)a.g * a.g * a.g;
-    const int64_t per = (total + 1023) / 1024;
-    const int64_t lo = threadIdx.x * per, hi = min(lo + per, total);
-    uint32_t s = 0;
-    for (int64_t i = lo; i < hi; i++) s += a.count[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < total; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < total ? a.count[i] : 0u;
+        uint32_t x = v;   // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if ((int)lane >= o) w += y;
+            }
+            wsum[lane] = w;   // inclusive over the warps
+        }
         __syncthreads();
+        if (i < total) {
+            a.start[i] = carry + (warp ? wsum[warp - 1] : 0u) + x - v;
+            a.cursor[i] = 0;
+        }
+        carry += wsum[31];
+        __syncthreads();   // wsum is rewritten next round
     }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int64_t i = lo; i < hi; i++) {
-        a.start[i] = run;
-        a.cursor[i] = 0;
-        run += a.count[i];
-    }
-    if (threadIdx.x == 1023) {
-        a.start[total] = part[1023];
-        if (part[1023] > a.cap) *a.overflow = 1u;
+    if (threadIdx.x == 0) {
+        a.start[total] = carry;
+        if (carry > a.cap) *a.overflow = 1u;
     }
 }
 
 __global__ void k_bin_fill(BinArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *a.n_moved || *a.overflow) return;
-    const int obj = a.moved[i];
-    int lo[3], hi[3];
-    box_cells(a, a.boxes + 6 * obj, lo, hi);
-    for (int z = lo[2]; z <= hi[2]; z++)
-        for (int y = lo[1]; y <= hi[1]; y++)
-            for (int x = lo[0]; x <= hi[0]; x++) {
-                const int c = x + a.g * (y + a.g * z);
-                a.items[a.start[c] + atomicAdd(a.cursor + c, 1u)] = obj;
-            }
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = (int)(threadIdx.x & 31);
+    if (w >= *a.n_moved || *a.overflow) return;
+    const int obj = a.moved[w];
+    int lo[3], n[3];
+    const int total = box_cell_range(a, a.boxes + 6 * obj, lo, n);
+    for (int i = lane; i < total; i += 32) {
+        const int x = lo[0] + i % n[0], y = lo[1] + (i / n[0]) % n[1], z = lo[2] + i / (n[0] * n[1]);
+        const int c = x + a.g * (y + a.g * z);
+        a.items[a.start[c] + atomicAdd(a.cursor + c, 1u)] = obj;
+    }
 }
 
 struct MaskArgs {
@@ -171,13 +192,13 @@ __global__ void __launch_bounds__(256) k_mask(MaskArgs a) {
     size_t v = 0;
     if (inside) {
         v = x + (size_t)n * (y + (size_t)n * z);
-        const uint32_t s = a.seeds[v];
+        const uint32_t s = __ldcs(a.seeds + v);
         if (s != SEED_EMPTY) {
             const int dx = (int)(s & 0xFF) - x, dy = (int)((s >> 8) & 0xFF) - y, dz = (int)((s >> 16) & 0xFF) - z;
             const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
             masked = d2 <= a.T;
         }
-        c = a.coarse[v];
+        c = __ldcs(a.coarse + v);
     }
     // warp-aggregated append of masked voxels
     const unsigned lane = threadIdx.x & 31;
@@ -197,12 +218,14 @@ __global__ void __launch_bounds__(256) k_mask(MaskArgs a) {
 #pragma unroll
         for (int dy = 0; dy < 2; dy++) {
             const size_t j = (size_t)2 * x + (size_t)nf * ((size_t)(2 * y + dy) + (size_t)nf * (2 * z + dz));
-            float2 u = *reinterpret_cast<const float2*>(a.accum + j);
+            // the fine grids stream through (each texel once per frame):
+            // cache-streaming accesses leave L2 to the tracer's BVH
+            float2 u = __ldcs(reinterpret_cast<const float2*>(a.accum + j));
             if (!masked) {
-                *reinterpret_cast<float2*>(a.fine + j) = make_float2(c, c);
+                __stcs(reinterpret_cast<float2*>(a.fine + j), make_float2(c, c));
                 if (u.x != CUDART_INF_F || u.y != CUDART_INF_F) {
-                    *reinterpret_cast<float2*>(a.accum + j) = make_float2(CUDART_INF_F, CUDART_INF_F);
-                    *reinterpret_cast<uint2*>(a.counts + j) = make_uint2(0u, 0u);
+                    __stcs(reinterpret_cast<float2*>(a.accum + j), make_float2(CUDART_INF_F, CUDART_INF_F));
+                    __stcs(reinterpret_cast<uint2*>(a.counts + j), make_uint2(0u, 0u));
                 }
                 continue;
             }
@@ -225,12 +248,12 @@ __global__ void __launch_bounds__(256) k_mask(MaskArgs a) {
                         un[dx] = __fadd_rn(__fmul_rn(a.alpha, un[dx]), __fmul_rn(1.f - a.alpha, c));
                 }
             }
-            if (un[0] != u.x || un[1] != u.y) *reinterpret_cast<float2*>(a.accum + j) = make_float2(un[0], un[1]);
+            if (un[0] != u.x || un[1] != u.y) __stcs(reinterpret_cast<float2*>(a.accum + j), make_float2(un[0], un[1]));
             if (clear[0] || clear[1]) {
-                uint2 cn = *reinterpret_cast<const uint2*>(a.counts + j);
+                uint2 cn = __ldcs(reinterpret_cast<const uint2*>(a.counts + j));
                 if (clear[0]) cn.x = 0u;
                 if (clear[1]) cn.y = 0u;
-                *reinterpret_cast<uint2*>(a.counts + j) = cn;
+                __stcs(reinterpret_cast<uint2*>(a.counts + j), cn);
             }
         }
     }
@@ -286,7 +309,7 @@ cudaError_t launch_mask(rtsdf_ctx* c, float d_vox) {
         const size_t cells = (size_t)b.g * b.g * b.g;
         if ((e = cudaMemsetAsync(c->bin_count, 0, cells * sizeof(uint32_t), c->stream))) return e;
         if ((e = cudaMemsetAsync(c->bin_overflow, 0, sizeof(uint32_t), c->stream))) return e;
-        const unsigned gb = (unsigned)((c->n_obj + 127) / 128);
+        const unsigned gb = (unsigned)((c->n_obj + 3) / 4);   // a warp per object, 4 per block
         RTSDF_LAUNCH(c, k_bin_count, gb, 128, 0, b);
         RTSDF_LAUNCH(c, k_bin_scan, 1, 1024, 0, b);
         RTSDF_LAUNCH(c, k_bin_fill, gb, 128, 0, b);
