@@ -133,11 +133,12 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
     }
 }
 
-// Eq. 1 per traced texel slot (see finalize_slot).
-__global__ void k_trace_finalize(TraceArgs a) {
-    const uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (s >= (uint64_t)(*a.count) * 8u) return;
-    finalize_slot(a, s);
+// Eq. 1 per traced texel slot (see finalize_slot): a grid-stride loop over
+// the frame's slots (8 per masked voxel, a count known only on the device).
+__global__ void __launch_bounds__(256) k_trace_finalize(TraceArgs a) {
+    const uint64_t n = (uint64_t)(*a.count) * 8u;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += stride) finalize_slot(a, s);
 }
 
 }  // namespace
@@ -192,8 +193,15 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     }
     if (c->counting) RTSDF_LAUNCH(c, k_trace<true>, c->trace_grid, TRACE_THREADS, 0, a);
     else RTSDF_LAUNCH(c, k_trace<false>, c->trace_grid, TRACE_THREADS, 0, a);
-    // one thread per possible slot; threads beyond the device count return
-    RTSDF_LAUNCH(c, k_trace_finalize, (unsigned)((8 * c->nc3 + 255) / 256), 256, 0, a);
+    // the slot count is on the device: enough blocks to fill every SM
+    // (8 x 256 threads each), capped by the largest possible slot count
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        const uint64_t most = (8 * (uint64_t)c->nc3 + 255) / 256;
+        const uint64_t want = (uint64_t)(sms > 0 ? sms : 132) * 8u;
+        RTSDF_LAUNCH(c, k_trace_finalize, (unsigned)(most < want ? most : want), 256, 0, a);
+    }
     return cudaGetLastError();
 }
 

@@ -367,6 +367,21 @@ __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool
     return active && ray_done(r);
 }
 
+// L2 policy for data that streams past the tracer (the per-slot scratch of
+// finished rays): evicted first, so that the BVH nodes and leaf triangles
+// the traversal re-reads keep their place in L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void red_min_stream(uint32_t* p, uint32_t v, uint64_t pol) {
+    asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_stream(uint32_t* p, uint32_t v, uint64_t pol) {
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
 // Commit of finished rays that share a texel slot (peers: the lanes of the
 // same slot among those finishing now; lt: lanes below this one).  Vote:
 // the minimum distance bits and the front | back << 16 hit counts.
@@ -378,7 +393,7 @@ __device__ __forceinline__ void commit_ray(const Ray& r, bool nearest, unsigned 
     if (nearest) {
         const uint32_t key = hit ? ((tbits << 1) | (r.bfront ? 0u : 1u)) : 0xFFFFFFFFu;
         const uint32_t mn = __reduce_min_sync(peers, key);
-        if ((peers & lt) == 0 && mn != 0xFFFFFFFFu) atomicMin(ray_min + r.slot, mn);
+        if ((peers & lt) == 0 && mn != 0xFFFFFFFFu) red_min_stream(ray_min + r.slot, mn, l2_evict_first());
         return;
     }
     const uint32_t tb = hit ? tbits : 0x7F800000u;
@@ -386,8 +401,9 @@ __device__ __forceinline__ void commit_ray(const Ray& r, bool nearest, unsigned 
     const uint32_t mn = __reduce_min_sync(peers, tb);
     const uint32_t sum = __reduce_add_sync(peers, cv);
     if ((peers & lt) == 0) {
-        if (mn != 0x7F800000u) atomicMin(ray_min + r.slot, mn);
-        if (sum) atomicAdd(ray_cnt + r.slot, sum);
+        const uint64_t pol = l2_evict_first();
+        if (mn != 0x7F800000u) red_min_stream(ray_min + r.slot, mn, pol);
+        if (sum) red_add_stream(ray_cnt + r.slot, sum, pol);
     }
 }
 
@@ -396,7 +412,9 @@ __device__ __forceinline__ void commit_ray(const Ray& r, bool nearest, unsigned 
 // (saturating at 16 bits), f_t = +-u_t or c_t while no ray has hit; the
 // slot's scratch is cleared for the next frame.
 __device__ __forceinline__ void finalize_slot(const TraceArgs& a, uint64_t s) {
-    const uint32_t parent = a.masked[s >> 3];
+    // every access here streams (each slot and texel is touched once per
+    // frame): cache-streaming loads and stores keep the BVH in L2
+    const uint32_t parent = __ldcs(a.masked + (s >> 3));
     const uint32_t ch = (uint32_t)(s & 7);
     const uint32_t nc = (uint32_t)a.nc, nf = 2u * nc;
     const uint32_t pq = __umulhi(parent, a.nc_mag), pz = __umulhi(pq, a.nc_mag);
@@ -405,33 +423,34 @@ __device__ __forceinline__ void finalize_slot(const TraceArgs& a, uint64_t s) {
     if (a.nearest) {
         // Eq. 1's minimum over (u, this frame's nearest hit), keeping the face
         // of the smaller one (counts holds the face: 1 = back)
-        const uint32_t km = a.ray_min[s];
-        a.ray_min[s] = ray_min_none(true);
-        const float u0 = a.accum[texel];
-        const uint32_t kp = u0 == CUDART_INF_F ? 0xFFFFFFFFu : ((__float_as_uint(u0) << 1) | (a.counts[texel] & 1u));
+        const uint32_t km = __ldcs(a.ray_min + s);
+        __stcs(a.ray_min + s, ray_min_none(true));
+        const float u0 = __ldcs(a.accum + texel);
+        const uint32_t kp =
+            u0 == CUDART_INF_F ? 0xFFFFFFFFu : ((__float_as_uint(u0) << 1) | (__ldcs(a.counts + texel) & 1u));
         const uint32_t k = min(kp, km);
         if (k == 0xFFFFFFFFu) {
-            a.fine[texel] = a.coarse[parent];
+            __stcs(a.fine + texel, __ldcs(a.coarse + parent));
             return;
         }
         const float u = __uint_as_float(k >> 1);
-        a.accum[texel] = u;
-        a.counts[texel] = k & 1u;
-        a.fine[texel] = (k & 1u) ? -u : u;
+        __stcs(a.accum + texel, u);
+        __stcs(a.counts + texel, k & 1u);
+        __stcs(a.fine + texel, (k & 1u) ? -u : u);
         return;
     }
-    const float rmin = __uint_as_float(a.ray_min[s]);
-    const uint32_t cv = a.ray_cnt[s];
-    a.ray_min[s] = ray_min_none(false);
-    a.ray_cnt[s] = 0u;
-    const float u = fminf(a.accum[texel], rmin);
-    const uint32_t cw = a.counts[texel];
+    const float rmin = __uint_as_float(__ldcs(a.ray_min + s));
+    const uint32_t cv = __ldcs(a.ray_cnt + s);
+    __stcs(a.ray_min + s, ray_min_none(false));
+    __stcs(a.ray_cnt + s, 0u);
+    const float u = fminf(__ldcs(a.accum + texel), rmin);
+    const uint32_t cw = __ldcs(a.counts + texel);
     const uint32_t f = min((cw & 0xFFFFu) + (cv & 0xFFFFu), 0xFFFFu);
     const uint32_t b = min((cw >> 16) + (cv >> 16), 0xFFFFu);
-    a.accum[texel] = u;
-    a.counts[texel] = f | (b << 16);
-    const float mag = u == CUDART_INF_F ? a.coarse[parent] : u;
-    a.fine[texel] = b > f ? -mag : mag;
+    __stcs(a.accum + texel, u);
+    __stcs(a.counts + texel, f | (b << 16));
+    const float mag = u == CUDART_INF_F ? __ldcs(a.coarse + parent) : u;
+    __stcs(a.fine + texel, b > f ? -mag : mag);
 }
 
 }  // namespace dev
