@@ -243,7 +243,15 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
         uint32_t* sd = b.sc[s].seeds[0];
         for (uint64_t g = tid; g < n3; g += nthr) sd[g] = SEED_EMPTY;
     }
-    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) *const_cast<uint32_t*>(b.sc[s].t.count) = 0u;
+    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) {
+        // the frame's ray parameters go into each scene's tracer fields, so
+        // that the trace stage reads them in place (no copy of the fields)
+        TraceArgs& t = const_cast<SceneDesc&>(b.sc[s]).t;
+        *const_cast<uint32_t*>(t.count) = 0u;
+        t.rays = P.rays;
+        t.log2_rays = P.log2_rays;
+        t.frame = P.frame;
+    }
     if (tid == 0) {
         *b.big_count = 0u;
         *b.next_ray = 0ull;
@@ -411,10 +419,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
                         const unsigned long long g = cn + rank;
                         const int scene = g < s_csend[wi] ? s_cscene[wi] : find_scene(s_rp, ns, g);
                         s_scene[threadIdx.x] = scene;
-                        TraceArgs ta = b.sc[scene].t;
-                        ta.rays = P.rays;
-                        ta.log2_rays = P.log2_rays;
-                        ta.frame = P.frame;
+                        const TraceArgs& ta = b.sc[scene].t;
                         setup_ray(ta, g - s_rp[scene], r);
                         // enter the scene's root in the concatenated tree
                         const SceneDesc& sd = b.sc[scene];
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
         const unsigned long long stot = s_rp[ns] >> lg;
         int sc = -1;
         unsigned long long lo = 0, hi = 0;   // slot range of scene sc
-        TraceArgs ta;
+        const TraceArgs* ta = nullptr;
         // thread index and count recomputed here, so that they are not
         // live through the trace stage
         const unsigned long long ftid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
@@ -469,9 +474,9 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
                 while ((s_rp[sc + 1] >> lg) <= g);
                 lo = s_rp[sc] >> lg;
                 hi = s_rp[sc + 1] >> lg;
-                ta = b.sc[sc].t;
+                ta = &b.sc[sc].t;
             }
-            finalize_slot(ta, g - lo);
+            finalize_slot(*ta, g - lo);
         }
     }
     grid_barrier(b);
