@@ -47,7 +47,13 @@ FLOP_PER_TEST = 30
 # an ncu capture of smsp__inst_executed.sum on one full-size launch (1 pass),
 # keyed like TRAFFIC below; the tracer's issue-roof fraction is computed from
 # it (null once the sources change).
-INST_PER_RAY = {}
+INST_PER_RAY = {
+    # ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+    # -k regex:k_trace -c 1 on "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant
+    # --no-configs" (1 pass; the first frame's launch, 409.84 ms): 394,441,291,176 warp instructions over
+    # 2,557,074 masked voxels x 8 texels x 64 rays = 1,309,221,888 rays
+    "2bfba22d031d6835": 301.28,
+}
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
 # by the sha256 of the sources it was measured on (the kernel and the BVH
@@ -57,6 +63,8 @@ TRAFFIC = {
     # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant" (1 pass), SAH tree:
     # 11.17 GB + 178.7 MB
     "be3e97993857e9f4": 11.1687e9 + 178.67e6,
+    # the same capture as INST_PER_RAY below: 11.12 GB + 177.83 MB
+    "2bfba22d031d6835": 11.12e9 + 177.83e6,
 }
 TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 
