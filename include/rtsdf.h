@@ -307,9 +307,11 @@ rtsdf_status rtsdf_jfa_noalloc(const uint32_t* seeds_in, uint32_t* seeds_out, fl
  * mesh, BVH) updated together.  rtsdf_batch_frame runs the whole per-frame
  * pipeline of Sec. 2.1-2.2 (voxelize, jump flood, mask, trace, Eq. 1) for
  * every scene in one persistent cooperative kernel launch, replayed from a
- * CUDA graph; each scene's result equals a plain per-scene frame (same
- * kernels' arithmetic, same rays).  Scenes must be static within the batch
- * (no pending rtsdf_move_objects).
+ * CUDA graph; with split_trace = 1 that launch stops after the mask and the
+ * trace and the Eq. 1 finalize of every scene follow as two launches of
+ * their own in the same graph.  Each scene's result equals a plain
+ * per-scene frame (same kernels' arithmetic, same rays).  Scenes must be
+ * static within the batch (no pending rtsdf_move_objects).
  * ------------------------------------------------------------------------ */
 typedef struct rtsdf_batch* rtsdf_batch_t;
 
@@ -321,6 +323,10 @@ typedef struct {
     int32_t barrier_spins;  /* polls before a grid-barrier wait gives up with RTSDF_E_TIMEOUT
                                (0 = default, about ten seconds) */
     int32_t leaf_min;       /* tracer: run the leaf phase once this many lanes hold a parked leaf */
+    int32_t split_trace;    /* 0: one persistent launch runs every stage; 1: that launch runs the
+                               pipeline up to the mask, and the trace and the Eq. 1 finalize follow
+                               as two launches of their own in the same frame (and graph), the
+                               trace at the per-scene tracer's occupancy; results are identical */
 } rtsdf_batch_tuning;
 
 typedef struct {
@@ -329,9 +335,10 @@ typedef struct {
     int32_t graph;          /* 1 when frames replay a captured graph */
     int64_t frames, launches;
     float last_frame_ms;    /* device time of the last frame (CUDA events) */
-    /* stage times of the last frame inside the persistent launch, ms (global
-       timer read at the stage barriers): clear, voxelize, large triangles,
-       jump flood, mask, trace, finalize */
+    /* stage times of the last frame, ms (global timer read at the stage
+       barriers; with split_trace, trace runs from the end of the pipeline
+       launch to the start of the finalize launch): clear, voxelize, large
+       triangles, jump flood, mask, trace, finalize */
     float stage_ms[7];
 } rtsdf_batch_info;
 

@@ -40,7 +40,7 @@ class Stats(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", c_i32), ("refill_min", c_i32), ("ray_chunk", c_i32), ("use_graph", c_i32),
-                ("barrier_spins", c_i32), ("leaf_min", c_i32)]
+                ("barrier_spins", c_i32), ("leaf_min", c_i32), ("split_trace", c_i32)]
 
 
 class Tuning(ctypes.Structure):

@@ -59,12 +59,15 @@ def _make_batch(items):
     return b
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_batch_equals_sequential(use_graph):
+@pytest.mark.parametrize("use_graph,split", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_batch_equals_sequential(use_graph, split):
+    # split = 1: the trace and the Eq. 1 finalize run as launches of their
+    # own after the pipeline launch; the grids must not change
     items = _workload()
     d, R, frames = 2.0, 8, [0, 1, 2]
     b = _make_batch(items)
-    b.set_tuning(use_graph=use_graph)
+    b.set_tuning(use_graph=use_graph, split_trace=split)
+    assert b.get_tuning()["split_trace"] == split
     for f in frames:
         b.frame(d, R, f)
     b.sync()
@@ -80,12 +83,15 @@ def test_batch_equals_sequential(use_graph):
     b.close()
 
 
-def test_batch_barrier_timeout_reported_then_recovers():
+@pytest.mark.parametrize("split", [0, 1])
+def test_batch_barrier_timeout_reported_then_recovers(split):
+    # with split = 1 the trace and finalize launches see the abort flag and
+    # skip their work
     from paper_2210_04449_gb300 import RtsdfError
     items = _workload()
     d, R = 2.0, 4
     b = _make_batch(items)
-    b.set_tuning(barrier_spins=1, use_graph=0)
+    b.set_tuning(barrier_spins=1, use_graph=0, split_trace=split)
     b.frame(d, R, 0)
     with pytest.raises(RtsdfError) as ei:
         b.sync()
@@ -171,6 +177,7 @@ def test_batch_matches_oracle():
     pick = [0, 1, 2, 6]
     d, R, frames = 2.0, 8, [0, 1, 2]
     b = _make_batch(items)
+    b.set_tuning(split_trace=1)
     for f in frames:
         b.frame(d, R, f)
     b.sync()
