@@ -662,13 +662,14 @@ def workload_config(nc, n_objects, n_tris):
             "coarse_n": nc, "fine_n": 2 * nc, "triangles": int(n_tris), "rays_per_texel": RAYS}
 
 
-def oracle_frame_sample(n_texels, seed=SEED, objects=N_OBJ, masked_texels=None):
+def oracle_frame_sample(n_texels, seed=SEED, objects=N_OBJ, masked_texels=None, brute_texels=16):
     """Time the oracle (as it stands) on one frame of the same workload:
     voxelize + jump flood + mask in full, then the closest hits of all 64
     rays of n_texels sampled masked texels through the oracle's hierarchy
     path (bit-identical to its brute force over all triangles, and the
     faster of its two), extrapolated to the frame's masked texels; returns
-    (ms/frame, details)."""
+    (ms/frame, details).  The details also time the brute-force path on
+    `brute_texels` of the same texels."""
     import numpy as np
 
     import oracle
@@ -692,13 +693,22 @@ def oracle_frame_sample(n_texels, seed=SEED, objects=N_OBJ, masked_texels=None):
     t4 = time.perf_counter()
     oracle.trace(mesh.verts, mesh.tris, B, 1.0, nf, seed, 1, RAYS, tex, accel="bvh")
     t5 = time.perf_counter()
+    # the brute-force path (every ray against every triangle) on a few of
+    # the same texels, for reference
+    nb = min(brute_texels, pick.size)
+    oracle.trace(mesh.verts, mesh.tris, B, 1.0, nf, seed, 1, RAYS, tex[:nb])
+    t6 = time.perf_counter()
     m_tex = masked.size * 8 if masked_texels is None else masked_texels
     per_texel = (t5 - t4) / max(pick.size, 1)
-    total = (t1 - t0) + (t2 - t1) + (t3 - t2) + per_texel * m_tex
+    per_texel_brute = (t6 - t5) / max(nb, 1)
+    coarse_s = (t1 - t0) + (t2 - t1) + (t3 - t2)
+    total = coarse_s + per_texel * m_tex
     return total * 1e3, {"voxelize_s": round(t1 - t0, 3), "jfa_s": round(t2 - t1, 3), "mask_s": round(t3 - t2, 3),
                          "trace_s_per_texel": round(per_texel, 7), "texels_sampled": int(pick.size),
-                         "masked_texels": int(m_tex), "sample_cpu_s": round(t5 - t0, 2),
-                         "triangles": int(mesh.nt)}
+                         "masked_texels": int(m_tex), "sample_cpu_s": round(t6 - t0, 2),
+                         "triangles": int(mesh.nt),
+                         "brute_force_trace_s_per_texel": round(per_texel_brute, 5), "brute_force_texels": int(nb),
+                         "brute_force_ms_per_frame": round((coarse_s + per_texel_brute * m_tex) * 1e3, 1)}
 
 
 def oracle_threads():

@@ -108,12 +108,14 @@ def test_batch_barrier_timeout_reported_then_recovers(split):
     b.close()
 
 
-def test_batch_nearest_face_variant_equals_sequential():
+@pytest.mark.parametrize("split", [0, 1])
+def test_batch_nearest_face_variant_equals_sequential(split):
     # scenes in the nearest-face mode (and one left in the vote mode) give the
     # grids of plain per-scene frames in the same modes
     items = _workload()
     d, R, frames = 2.0, 8, [0, 1, 2]
     b = _make_batch(items)
+    b.set_tuning(split_trace=split)
     for i, sc in enumerate(b.scenes):
         if i != 2:
             sc.set_sign_mode("nearest")
@@ -137,7 +139,8 @@ def test_batch_nearest_face_variant_equals_sequential():
     b.close()
 
 
-def test_batch_with_any_builder_and_a_one_triangle_scene():
+@pytest.mark.parametrize("split", [0, 1])
+def test_batch_with_any_builder_and_a_one_triangle_scene(split):
     # scenes built by every builder (the animated one two-level, over its
     # objects) plus a scene of a single triangle: the grids of plain frames
     from paper_2210_04449_gb300 import RTSDFBatch
@@ -146,6 +149,7 @@ def test_batch_with_any_builder_and_a_one_triangle_scene():
     items = _workload() + [(dict(coarse_n=16, beta_vox=0.5, seed=8), one)]
     d, R, frames = 2.0, 8, [0, 1]
     b = RTSDFBatch([cfg for cfg, _ in items])
+    b.set_tuning(split_trace=split)
     builders = ["sah", "lbvh", "two_level", "lbvh", "sah", "two_level", "two_level", "sah"]
     for i, (sc, (_, mesh)) in enumerate(zip(b.scenes, items)):
         sc.set_bvh_builder(builders[i])
