@@ -140,6 +140,17 @@ rtsdf_status rtsdf_set_objects(rtsdf_t ctx, const int32_t* vert_object, int32_t 
  * next rtsdf_sync and are clamped. */
 rtsdf_status rtsdf_move_objects(rtsdf_t ctx, const float* translations, int on_device);
 
+/* Moves every object by a rigid transform (float32 [n_objects][3][4], rows
+ * of [R | t], host or device pointer): v' = R v + t in fp32 with each
+ * product and sum rounded in the order v'_a = ((R_a0 x + R_a1 y) + R_a2 z)
+ * + t_a (no fused multiply-add), so a caller can reproduce the positions
+ * exactly.  An object whose transform is exactly the identity does not
+ * move; the others are handled as in rtsdf_move_objects (their previous
+ * bounding boxes drive the reset in changed regions at the next trace).
+ * Vertices that leave the accepted box set RTSDF_E_MESH at the next
+ * rtsdf_sync and are clamped. */
+rtsdf_status rtsdf_transform_objects(rtsdf_t ctx, const float* xforms, int on_device);
+
 /* Builds (refit = 0) a binary BVH over the uploaded triangles, one triangle
  * per leaf, collapsed to 4-wide nodes for the tracer, or recomputes its
  * boxes for the current vertex positions keeping the topology (refit = 1;

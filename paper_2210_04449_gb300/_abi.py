@@ -64,6 +64,7 @@ SIGNATURES = {
     "rtsdf_upload_mesh": (status_t, [ctx_t, c_vp, c_i64, c_vp, c_i64, c_int]),
     "rtsdf_set_objects": (status_t, [ctx_t, c_vp, c_i32, c_int]),
     "rtsdf_move_objects": (status_t, [ctx_t, c_vp, c_int]),
+    "rtsdf_transform_objects": (status_t, [ctx_t, c_vp, c_int]),
     "rtsdf_build_bvh": (status_t, [ctx_t, c_int]),
     "rtsdf_voxelize": (status_t, [ctx_t]),
     "rtsdf_jfa": (status_t, [ctx_t]),

@@ -127,6 +127,13 @@ class RTSDF:
         call("rtsdf_move_objects", self._h, p, d)
         self._keep = k   # device buffers must outlive the enqueued copy
 
+    def transform_objects(self, xforms) -> None:
+        """Rigid transform per object: float32 [n_objects, 3, 4] (rows of
+        [R | t]) or [n_objects, 12]; see rtsdf_transform_objects."""
+        p, d, k = _host_or_device(xforms, np.float32)
+        call("rtsdf_transform_objects", self._h, p, d)
+        self._keep = k   # device buffers must outlive the enqueued copy
+
     def build_bvh(self, refit: bool = False) -> None:
         call("rtsdf_build_bvh", self._h, int(bool(refit)))
 

@@ -72,7 +72,7 @@ void dfree(T*& p) {
 
 void free_all(rtsdf_ctx* c) {
     dfree(c->verts); dfree(c->qverts); dfree(c->tris); dfree(c->vert_obj); dfree(c->obj_box);
-    dfree(c->obj_trans); dfree(c->moved_list); dfree(c->d_moved_count);
+    dfree(c->obj_trans); dfree(c->obj_xform); dfree(c->moved_list); dfree(c->d_moved_count);
     dfree(c->seeds[0]); dfree(c->seeds[1]); dfree(c->coarse); dfree(c->big_list); dfree(c->d_big_count);
     dfree(c->accum); dfree(c->counts); dfree(c->fine); dfree(c->masked); dfree(c->d_masked_count);
     dfree(c->ray_min); dfree(c->ray_cnt); dfree(c->d_next_ray);
@@ -298,10 +298,10 @@ rtsdf_status rtsdf_set_objects(rtsdf_t c, const int32_t* vert_object, int32_t n_
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e) return from_cuda(e);
     if (n_objects > c->cap_obj) {
-        dfree(c->obj_box); dfree(c->obj_trans); dfree(c->moved_list);
+        dfree(c->obj_box); dfree(c->obj_trans); dfree(c->obj_xform); dfree(c->moved_list);
         c->cap_obj = 0;
         if ((e = dalloc(&c->obj_box, 6 * (size_t)n_objects)) || (e = dalloc(&c->obj_trans, 3 * (size_t)n_objects)) ||
-            (e = dalloc(&c->moved_list, (size_t)n_objects)))
+            (e = dalloc(&c->obj_xform, 12 * (size_t)n_objects)) || (e = dalloc(&c->moved_list, (size_t)n_objects)))
             return from_cuda(e);
         c->cap_obj = n_objects;
     }
@@ -334,6 +334,22 @@ rtsdf_status rtsdf_move_objects(rtsdf_t c, const float* translations, int on_dev
     cudaError_t e = cudaMemcpyAsync(c->obj_trans, translations, sizeof(float) * 3 * c->n_obj,
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
     if (!e) e = launch_move(c);
+    if (!e) e = launch_quantise(c);
+    if (e) return from_cuda(e);
+    c->voxelized = c->flooded = false;
+    c->bvh_dirty = true;
+    c->reset_pending = true;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_transform_objects(rtsdf_t c, const float* xforms, int on_device) {
+    if (!c || !xforms) return RTSDF_E_ARG;
+    if (!c->have_mesh || c->n_obj < 1) return RTSDF_E_STATE;
+    DeviceGuard g(c->device);
+    StageTimer tm(c, ST_MOTION);
+    cudaError_t e = cudaMemcpyAsync(c->obj_xform, xforms, sizeof(float) * 12 * c->n_obj,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = launch_transform(c);
     if (!e) e = launch_quantise(c);
     if (e) return from_cuda(e);
     c->voxelized = c->flooded = false;

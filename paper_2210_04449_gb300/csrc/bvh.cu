@@ -375,6 +375,51 @@ __global__ void k_translate(float* __restrict__ verts, const int32_t* __restrict
     verts[i] = __fadd_rn(verts[i], trans[3 * vobj[v] + a]);
 }
 
+// Rigid transforms, rows of [R | t] per object (12 floats).  An object is
+// moved unless its transform is exactly the identity.
+__device__ __forceinline__ bool xform_moves(const float* m) {
+    return m[0] != 1.f || m[1] != 0.f || m[2] != 0.f || m[3] != 0.f || m[4] != 0.f || m[5] != 1.f ||
+           m[6] != 0.f || m[7] != 0.f || m[8] != 0.f || m[9] != 0.f || m[10] != 1.f || m[11] != 0.f;
+}
+
+__global__ void k_moved_list_x(const float* __restrict__ xf, int n_obj, int32_t* list, int32_t* count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_obj) return;
+    if (xform_moves(xf + 12 * i)) list[atomicAdd(count, 1)] = i;
+}
+
+// Box of every moved object before the transform.
+__global__ void k_obj_boxes_x(const float* __restrict__ verts, const int32_t* __restrict__ vobj, int64_t nv,
+                              const float* __restrict__ xf, float* boxes) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    const int o = vobj[i];
+    if (!xform_moves(xf + 12 * o)) return;
+    for (int a = 0; a < 3; a++) {
+        atomic_min_f(boxes + 6 * o + a, verts[3 * i + a]);
+        atomic_max_f(boxes + 6 * o + 3 + a, verts[3 * i + a]);
+    }
+}
+
+// v' = R v + t in fp32, each product and sum rounded in this order:
+// v'_a = ((R_a0 x + R_a1 y) + R_a2 z) + t_a  (no fused multiply-add).
+__global__ void k_transform(float* __restrict__ verts, const int32_t* __restrict__ vobj, int64_t nv,
+                            const float* __restrict__ xf) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    const float* m = xf + 12 * vobj[i];
+    const float x = verts[3 * i], y = verts[3 * i + 1], z = verts[3 * i + 2];
+    float out[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float* r = m + 4 * a;
+        out[a] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)), __fmul_rn(r[2], z)), r[3]);
+    }
+    verts[3 * i] = out[0];
+    verts[3 * i + 1] = out[1];
+    verts[3 * i + 2] = out[2];
+}
+
 }  // namespace
 
 // Collapse the binary tree into 4-wide nodes, on the device, one tree level
@@ -730,6 +775,22 @@ cudaError_t launch_move(rtsdf_ctx* c) {
                      c->obj_trans, c->obj_box);
         RTSDF_LAUNCH(c, k_translate, (unsigned)((c->nv * 3 + 255) / 256), 256, 0, c->verts, c->vert_obj, c->nv,
                      c->obj_trans);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transform(rtsdf_ctx* c) {
+    const int n_obj = c->n_obj;
+    cudaError_t e = cudaMemsetAsync(c->d_moved_count, 0, sizeof(int32_t), c->stream);
+    if (e != cudaSuccess) return e;
+    RTSDF_LAUNCH(c, k_obj_boxes_init, (n_obj + 127) / 128, 128, 0, c->obj_box, n_obj);
+    RTSDF_LAUNCH(c, k_moved_list_x, (n_obj + 127) / 128, 128, 0, c->obj_xform, n_obj, c->moved_list,
+                 c->d_moved_count);
+    if (c->nv > 0) {
+        RTSDF_LAUNCH(c, k_obj_boxes_x, (unsigned)((c->nv + 255) / 256), 256, 0, c->verts, c->vert_obj, c->nv,
+                     c->obj_xform, c->obj_box);
+        RTSDF_LAUNCH(c, k_transform, (unsigned)((c->nv + 255) / 256), 256, 0, c->verts, c->vert_obj, c->nv,
+                     c->obj_xform);
     }
     return cudaGetLastError();
 }

@@ -154,6 +154,7 @@ struct rtsdf_ctx {
     int n_obj = 0, cap_obj = 0;
     float* obj_box = nullptr;     // [n_obj * 6] box before the last move (lo xyz, hi xyz)
     float* obj_trans = nullptr;   // [n_obj * 3]
+    float* obj_xform = nullptr;   // [n_obj * 12] rigid transforms (rtsdf_transform_objects), rows of [R | t]
     int32_t* moved_list = nullptr;// [n_obj] objects with a non-zero translation
     int32_t* d_moved_count = nullptr;
     bool reset_pending = false;
@@ -228,6 +229,7 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame);
 cudaError_t launch_bvh_build(rtsdf_ctx* c);
 cudaError_t launch_bvh_refit(rtsdf_ctx* c);
 cudaError_t launch_move(rtsdf_ctx* c);
+cudaError_t launch_transform(rtsdf_ctx* c);
 cudaError_t launch_shadow(rtsdf_ctx* c, const float* sdf, const float* pos, const float* nrm,
                           int64_t npix, const float L[3], float k, int steps, float smax,
                           float eps, float jitter, int frame, float* vis);

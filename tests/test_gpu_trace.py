@@ -212,6 +212,62 @@ def test_motion_refit_and_reset():
     _compare(rt, pipe, None, "motion")
 
 
+def _rotation(axis, angle):
+    a = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * (K @ K)
+
+
+def test_rigid_transforms_and_reset():
+    # rtsdf_transform_objects: every object except each third one turns by
+    # up to 5 degrees about its own centre and moves by up to half a coarse
+    # voxel; the oracle gets the vertices computed in numpy float32 with the
+    # documented operation order ((R0 x + R1 y) + R2 z) + t, and the boxes
+    # of the moved objects before the move for the reset rule
+    from paper_2210_04449_gb300 import RTSDF
+    mesh = S.animated_scene(4, n_objects=12, n_lon=16, n_lat=9)
+    nc, d, beta, R = 32, 2.0, 0.5, 8
+    n_obj = mesh.n_objects
+    rt = RTSDF(nc, beta_vox=beta, seed=9)
+    rt.upload_mesh(mesh.verts, mesh.tris)
+    rt.set_objects(mesh.vert_object, n_obj)
+    rt.build_bvh()
+    verts = mesh.verts.copy()
+    pipe = oracle.FinePipeline(BMIN, 1.0, nc, beta, d, 1.0, 9)
+    rng = np.random.default_rng(3)
+    moved = None
+    for t in range(4):
+        if t > 0:
+            xf = np.zeros((n_obj, 3, 4), np.float32)
+            xf[:, :, :3] = np.eye(3, dtype=np.float32)
+            for k in range(n_obj):
+                if k % 3 == 0:
+                    continue                                  # exactly the identity: stays
+                c = verts[mesh.vert_object == k].astype(np.float64).mean(0)
+                Rm = _rotation(rng.normal(size=3), np.radians(rng.uniform(-5, 5)))
+                step = rng.uniform(-1, 1, 3) * 0.5 / nc / np.sqrt(3)
+                xf[k, :, :3] = Rm
+                xf[k, :, 3] = c - Rm @ c + step
+            mv = np.array([k % 3 != 0 for k in range(n_obj)])
+            lo = np.stack([verts[mesh.vert_object == k].min(0) for k in range(n_obj)])
+            hi = np.stack([verts[mesh.vert_object == k].max(0) for k in range(n_obj)])
+            moved = (lo[mv], hi[mv])
+            M = xf[mesh.vert_object]                          # [nv, 3, 4] float32
+            x, y, z = verts[:, 0:1], verts[:, 1:2], verts[:, 2:3]
+            verts = (((M[:, :, 0] * x + M[:, :, 1] * y) + M[:, :, 2] * z) + M[:, :, 3]).astype(np.float32)
+            rt.transform_objects(xf)
+            rt.build_bvh(refit=True)
+        rt.update(d, R, t)
+        out = pipe.frame(verts, mesh.tris, t, R, moved_aabbs=moved)
+    rt.sync()
+    # the same vertices on both sides: the voxels and seeds agree bit for bit
+    occ_g = rt.grids()["seeds"].cpu().numpy()
+    from tests._util import seeds_to_linear
+    assert np.array_equal(seeds_to_linear(occ_g, nc), out["seeds"])
+    _compare(rt, pipe, None, "rigid transforms")
+    assert np.isfinite(pipe.u).sum() > 10_000          # texels with an accumulated distance
+
+
 def test_checkpoint_resume_is_bit_identical():
     from paper_2210_04449_gb300 import RTSDF
     m = S.tiny_scene()
