@@ -151,6 +151,15 @@ rtsdf_status rtsdf_move_objects(rtsdf_t ctx, const float* translations, int on_d
  * rtsdf_sync and are clamped. */
 rtsdf_status rtsdf_transform_objects(rtsdf_t ctx, const float* xforms, int on_device);
 
+/* Reset in changed regions on (1, default) or off (0).  The paper keeps
+ * moving objects' old distances from persisting only through the temporal
+ * weight alpha of Eq. 1 (Sec. 2.2); with the reset off, moves leave the
+ * accumulation alone and alpha < 1 is what lets stale minima fade.
+ * Turning it off drops a reset already scheduled by a move.  RTSDF_E_ARG
+ * for any other value. */
+rtsdf_status rtsdf_set_reset(rtsdf_t ctx, int32_t on);
+rtsdf_status rtsdf_get_reset(rtsdf_t ctx, int32_t* on);
+
 /* Builds (refit = 0) a binary BVH over the uploaded triangles, one triangle
  * per leaf, collapsed to 4-wide nodes for the tracer, or recomputes its
  * boxes for the current vertex positions keeping the topology (refit = 1;

@@ -65,6 +65,8 @@ SIGNATURES = {
     "rtsdf_set_objects": (status_t, [ctx_t, c_vp, c_i32, c_int]),
     "rtsdf_move_objects": (status_t, [ctx_t, c_vp, c_int]),
     "rtsdf_transform_objects": (status_t, [ctx_t, c_vp, c_int]),
+    "rtsdf_set_reset": (status_t, [ctx_t, c_i32]),
+    "rtsdf_get_reset": (status_t, [ctx_t, ctypes.POINTER(c_i32)]),
     "rtsdf_build_bvh": (status_t, [ctx_t, c_int]),
     "rtsdf_voxelize": (status_t, [ctx_t]),
     "rtsdf_jfa": (status_t, [ctx_t]),

@@ -134,6 +134,15 @@ class RTSDF:
         call("rtsdf_transform_objects", self._h, p, d)
         self._keep = k   # device buffers must outlive the enqueued copy
 
+    def set_reset(self, on: bool) -> None:
+        """Reset in changed regions after moves (default on); see rtsdf_set_reset."""
+        call("rtsdf_set_reset", self._h, int(bool(on)))
+
+    def get_reset(self) -> bool:
+        v = ctypes.c_int32()
+        call("rtsdf_get_reset", self._h, ctypes.byref(v))
+        return bool(v.value)
+
     def build_bvh(self, refit: bool = False) -> None:
         call("rtsdf_build_bvh", self._h, int(bool(refit)))
 

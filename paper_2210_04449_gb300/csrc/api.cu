@@ -338,7 +338,7 @@ rtsdf_status rtsdf_move_objects(rtsdf_t c, const float* translations, int on_dev
     if (e) return from_cuda(e);
     c->voxelized = c->flooded = false;
     c->bvh_dirty = true;
-    c->reset_pending = true;
+    c->reset_pending = c->reset_on;
     return RTSDF_OK;
 }
 
@@ -354,7 +354,7 @@ rtsdf_status rtsdf_transform_objects(rtsdf_t c, const float* xforms, int on_devi
     if (e) return from_cuda(e);
     c->voxelized = c->flooded = false;
     c->bvh_dirty = true;
-    c->reset_pending = true;
+    c->reset_pending = c->reset_on;
     return RTSDF_OK;
 }
 
@@ -628,6 +628,19 @@ rtsdf_status rtsdf_set_sign_mode(rtsdf_t c, int32_t mode) {
 rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
     if (!c || !mode) return RTSDF_E_ARG;
     *mode = c->sign_mode;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_set_reset(rtsdf_t c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return RTSDF_E_ARG;
+    c->reset_on = on != 0;
+    if (!c->reset_on) c->reset_pending = false;
+    return RTSDF_OK;
+}
+
+rtsdf_status rtsdf_get_reset(rtsdf_t c, int32_t* on) {
+    if (!c || !on) return RTSDF_E_ARG;
+    *on = c->reset_on ? 1 : 0;
     return RTSDF_OK;
 }
 

@@ -158,6 +158,7 @@ struct rtsdf_ctx {
     int32_t* moved_list = nullptr;// [n_obj] objects with a non-zero translation
     int32_t* d_moved_count = nullptr;
     bool reset_pending = false;
+    bool reset_on = true;         // rtsdf_set_reset: moves schedule the reset in changed regions
     // moved boxes binned on a coarse cell grid for the reset test
     uint32_t* bin_count = nullptr;
     uint32_t* bin_start = nullptr;
