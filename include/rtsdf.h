@@ -160,6 +160,14 @@ rtsdf_status rtsdf_transform_objects(rtsdf_t ctx, const float* xforms, int on_de
 rtsdf_status rtsdf_set_reset(rtsdf_t ctx, int32_t on);
 rtsdf_status rtsdf_get_reset(rtsdf_t ctx, int32_t* on);
 
+/* Test hook for the allocation-failure paths (not a step of the paper):
+ * after `after` more device allocations of a context (grids, mesh, BVH and
+ * tracer buffers) succeed, the next one fails as if the device were out of
+ * memory, without calling the allocator; the call that made it returns
+ * RTSDF_E_OOM, frees what it had allocated, and the hook turns itself off.
+ * after < 0 turns it off.  Process-wide; for tests only. */
+void rtsdf_debug_fail_allocation(int64_t after);
+
 /* Builds (refit = 0) a binary BVH over the uploaded triangles, one triangle
  * per leaf, collapsed to 4-wide nodes for the tracer, or recomputes its
  * boxes for the current vertex positions keeping the topology (refit = 1;

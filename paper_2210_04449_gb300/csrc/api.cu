@@ -1,6 +1,7 @@
 // extern "C" entry points of librtsdf: argument checks, the call-order state
 // machine, device memory ownership, the device status word and per-stage
 // timing.  The numerical work is in the stage translation units.
+#include <atomic>
 #include <math.h>
 #include <math_constants.h>
 #include <stdlib.h>
@@ -58,9 +59,21 @@ __global__ void k_check_objects(const int32_t* vobj, int64_t nv, int n_obj, uint
     fixed[i] = o;
 }
 
+// Allocation-failure injection for tests (rtsdf_debug_fail_allocation):
+// the number of device allocations that still succeed before one fails,
+// -1 when off.
+std::atomic<long long> g_fail_after{-1};
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
     *p = nullptr;
+    long long k = g_fail_after.load();
+    while (k >= 0) {
+        if (g_fail_after.compare_exchange_weak(k, k - 1)) {
+            if (k == 0) return cudaErrorMemoryAllocation;   // the injected failure (the hook is now off)
+            break;
+        }
+    }
     return cudaMalloc((void**)p, count > 0 ? count * sizeof(T) : 16);
 }
 
@@ -258,6 +271,14 @@ rtsdf_status rtsdf_upload_mesh(rtsdf_t c, const float* verts, int64_t nv, const 
     DeviceGuard g(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e) return from_cuda(e);
+    // the old mesh is gone from here on, also when an allocation below fails
+    c->have_mesh = false;
+    c->nv = c->nt = 0;
+    c->n_obj = 0;
+    c->voxelized = c->flooded = false;
+    c->bvh.built = false;
+    c->bvh_dirty = true;
+    c->reset_pending = false;
     if (nv > c->cap_v) {
         dfree(c->verts); dfree(c->qverts); dfree(c->vert_obj);
         c->cap_v = 0;
@@ -630,6 +651,8 @@ rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
     *mode = c->sign_mode;
     return RTSDF_OK;
 }
+
+void rtsdf_debug_fail_allocation(int64_t after) { g_fail_after.store(after < 0 ? -1 : (long long)after); }
 
 rtsdf_status rtsdf_set_reset(rtsdf_t c, int32_t on) {
     if (!c || (on != 0 && on != 1)) return RTSDF_E_ARG;

@@ -133,3 +133,25 @@ def test_motion_leaving_the_volume_is_reported_and_cleared():
     assert _name(rt.sync) == "RTSDF_E_MESH"               # clamped, reported once
     rt.sync()                                             # the status word was cleared
     rt.close()
+
+
+def test_allocation_failure_returns_oom_and_recovers():
+    # host-side fault injection: the context allocator fails the n-th
+    # allocation (no device allocation is attempted for it); the call returns
+    # RTSDF_E_OOM and frees what it allocated, and everything works again
+    from paper_2210_04449_gb300 import RTSDF, _abi
+    lib = _abi.lib()
+    m = S.tiny_scene()
+    ref = _fine_after_frame(RTSDF(16, seed=1), m)
+    for after in (0, 3, 12):
+        lib.rtsdf_debug_fail_allocation(after)
+        assert _name(RTSDF, 16, seed=1) == "RTSDF_E_OOM"
+    lib.rtsdf_debug_fail_allocation(-1)
+    rt = RTSDF(16, seed=1)
+    # fail inside the mesh upload (its vertex / index buffers), then retry
+    lib.rtsdf_debug_fail_allocation(0)
+    assert _name(rt.upload_mesh, m.verts, m.tris) == "RTSDF_E_OOM"
+    lib.rtsdf_debug_fail_allocation(-1)
+    assert np.array_equal(_fine_after_frame(rt, m), ref)
+    rt.sync()
+    rt.close()
