@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <new>
+#include <nvtx3/nvToolsExt.h>
 #include <vector>
 
 #include "internal.cuh"
@@ -138,11 +139,19 @@ void drain(Timer& t) {
     t.n = 0;
 }
 
+// Each stage call is also an NVTX range (named for profilers such as ncu's
+// range filters; the header-only NVTX v3 API costs a pointer test when no
+// tool is attached).
+const char* const kStageRange[ST_COUNT] = {"rtsdf voxelize", "rtsdf jfa", "rtsdf mask",   "rtsdf trace",
+                                           "rtsdf bvh",      "rtsdf shadow", "rtsdf shadow backward",
+                                           "rtsdf motion"};
+
 struct StageTimer {
     rtsdf_ctx* c;
     Stage s;
     int slot = -1;
     StageTimer(rtsdf_ctx* ctx, Stage st) : c(ctx), s(st) {
+        nvtxRangePushA(kStageRange[s]);
         if (!c->profiling) return;
         Timer& t = c->timers[s];
         if (t.n == TIMER_RING) drain(t);
@@ -150,6 +159,7 @@ struct StageTimer {
         cudaEventRecord(t.a[slot], c->stream);
     }
     ~StageTimer() {
+        nvtxRangePop();
         if (slot < 0) return;
         Timer& t = c->timers[s];
         cudaEventRecord(t.b[slot], c->stream);
