@@ -516,8 +516,12 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
 // its speed: the traversal is issue bound and hides latency with warps),
 // then the finalize; both follow the pipeline launch on the stream and skip
 // their work when that launch gave up at a barrier.
+// (The bound asks for 8 resident blocks, i.e. at most 64 registers, as the
+// per-scene tracer's does; the kernel compiles to 56 and runs 9 blocks per
+// SM.  Asking for 9 forces 55 registers and code that issues 4 % more
+// instructions per ray.)
 #ifndef BATCH_TRACE_BLOCKS_PER_SM
-#define BATCH_TRACE_BLOCKS_PER_SM 9
+#define BATCH_TRACE_BLOCKS_PER_SM 8
 #endif
 
 __global__ void __launch_bounds__(TRACE_THREADS, BATCH_TRACE_BLOCKS_PER_SM) k_batch_trace(BatchArgs b) {
