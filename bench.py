@@ -50,21 +50,18 @@ FLOP_PER_TEST = 30
 INST_PER_RAY = {
     # ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     # -k regex:k_trace -c 1 on "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant
-    # --no-configs" (1 pass; the first frame's launch, 409.84 ms): 394,441,291,176 warp instructions over
+    # --no-configs" (1 pass; the first frame's launch, 409.71 ms): 394,441,834,694 warp instructions over
     # 2,557,074 masked voxels x 8 texels x 64 rays = 1,309,221,888 rays
-    "2bfba22d031d6835": 301.28,
+    "733479c010d8cc64": 301.28,
 }
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
 # by the sha256 of the sources it was measured on (the kernel and the BVH
 # builders, whose tree it walks); reported as null once any of them changes.
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first k_trace<0> launch of
-    # "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant" (1 pass), SAH tree:
-    # 11.17 GB + 178.7 MB
-    "be3e97993857e9f4": 11.1687e9 + 178.67e6,
-    # the same capture as INST_PER_RAY below: 11.12 GB + 177.83 MB
-    "2bfba22d031d6835": 11.12e9 + 177.83e6,
+    # the same capture as INST_PER_RAY above (first k_trace<0> launch, SAH tree): 11.11 GB read +
+    # 176.23 MB written
+    "733479c010d8cc64": 11.11e9 + 176.23e6,
 }
 TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 
