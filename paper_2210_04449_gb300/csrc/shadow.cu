@@ -328,11 +328,12 @@ __global__ void __launch_bounds__(dev::TRACE_THREADS) k_shadow_exact(dev::TraceA
     r.slot = 0;
     r.steps = 0;
     uint32_t nv = 0, ntest = 0;
-    // every step enters a node or tests a leaf (bounded by the node steps'
-    // own guard); the loop ends at the first hit or when nothing is left
+    // every step enters a node or tests a leaf (bounded by the step guard);
+    // the loop ends at the first hit or when nothing is left
     while (r.bidx == 0x7FFFFFFF && !dev::ray_done(r)) {
         dev::node_step<false>(t, r, stk, nv);
         if (r.leaf != WIDE_EMPTY) dev::leaf_step<false>(t, r, stk, nv, ntest);
+        dev::step_guard(t, r);
     }
     const bool b = r.bidx != 0x7FFFFFFF;
     if (blocked) blocked[i] = (uint8_t)b;

@@ -213,27 +213,38 @@ struct Stack {
 // triangle tests does not change the closest hit (every triangle whose box
 // the ray meets is tested unless its entry distance exceeds the best hit).
 
-// next stack entry that can still hold a hit at distance <= bt (WIDE_EMPTY: none)
-__device__ __forceinline__ int pop_next(Ray& r, Stack& stack) {
+// Pop the next entry that can still hold a hit at distance <= bt, parking
+// leaves while the lane's slot is free; stops at an internal node, at a leaf
+// behind the parked one, or with the stack empty (r.node = WIDE_EMPTY).
+__device__ __forceinline__ void advance(Ray& r, Stack& stack) {
+    int nx = WIDE_EMPTY;
     while (r.sp > 0) {
-        int nx;
+        int cand;
         float te;
-        stack.pop(--r.sp, nx, te);
-        if (te <= r.bt) return nx;
+        stack.pop(--r.sp, cand, te);
+        if (te > r.bt) continue;
+        if (cand < 0 && r.leaf == WIDE_EMPTY) {
+            r.leaf = ~cand;
+            continue;
+        }
+        nx = cand;
+        break;
     }
-    return WIDE_EMPTY;
-}
-
-// while the next node is a leaf and no leaf is parked, park it and go on
-// with the next stack entry
-__device__ __forceinline__ void park_leaves(Ray& r, Stack& stack) {
-    while (r.node != WIDE_EMPTY && r.node < 0 && r.leaf == WIDE_EMPTY) {
-        r.leaf = ~r.node;
-        r.node = pop_next(r, stack);
-    }
+    r.node = nx;
 }
 
 __device__ __forceinline__ bool ray_done(const Ray& r) { return r.node == WIDE_EMPTY && r.leaf == WIDE_EMPTY; }
+
+// A damaged tree (a cycle) would make a walk endless: a lane whose walk has
+// taken more node and leaf steps than a tree of 2 nt - 1 nodes allows stops,
+// and the call reports ERR_STACK.  Checked once per traversal iteration.
+template <class A>
+__device__ __forceinline__ void step_guard(const A& a, Ray& r) {
+    if (r.steps > 2u * (uint32_t)a.nt + 2u) {
+        atomicOr(a.err, ERR_STACK);
+        r.node = r.leaf = WIDE_EMPTY;
+    }
+}
 
 // Enter r.node if it is an internal node (A: any argument block with the BVH
 // fields wide, tri, nt and err).
@@ -241,11 +252,7 @@ template <bool COUNT, class A>
 __device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint32_t& visits) {
     const int node = r.node;
     if (node < 0) return;   // none, or a leaf waiting behind the parked one
-    if (++r.steps > 2u * (uint32_t)a.nt + 2u) {   // only a damaged tree gets here
-        atomicOr(a.err, ERR_STACK);
-        r.node = r.leaf = WIDE_EMPTY;
-        return;
-    }
+    r.steps++;
     if (COUNT) visits++;
     // 4-wide node: test the four child boxes, visit the nearest hit child
     // next and push the others farthest-first with their entry distance.
@@ -282,27 +289,31 @@ __device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint
         key[k] = hit ? t0 : CUDART_INF_F;
         nh += hit;
     }
-    if (nh > 0) {
-        // ascending sort of (key, val): a 5-exchange network
+    // ascending sort of (key, val) by a 5-exchange network, done whether or
+    // not a child was hit (a branch around it costs more than it saves)
 #define RTSDF_CAS(i, j)                                                     \
     if (key[j] < key[i]) {                                                  \
         const float tk = key[i]; key[i] = key[j]; key[j] = tk;              \
         const int tv = val[i]; val[i] = val[j]; val[j] = tv;                \
     }
-        RTSDF_CAS(0, 1) RTSDF_CAS(2, 3) RTSDF_CAS(0, 2) RTSDF_CAS(1, 3) RTSDF_CAS(1, 2)
+    RTSDF_CAS(0, 1) RTSDF_CAS(2, 3) RTSDF_CAS(0, 2) RTSDF_CAS(1, 3) RTSDF_CAS(1, 2)
 #undef RTSDF_CAS
+    // a nearest child that is a leaf is parked at once when the lane's slot
+    // is free, and the next nearest is entered without a round trip through
+    // the stack
+    const int first = (nh > 0 && val[0] < 0 && r.leaf == WIDE_EMPTY) ? 1 : 0;
+    if (first) r.leaf = ~val[0];
 #pragma unroll
-        for (int k = 3; k >= 1; k--) {
-            if (k < nh) {
-                if (r.sp < TRACE_STACK) stack.push(r.sp++, val[k], key[k]);
-                else atomicOr(a.err, ERR_STACK);
-            }
+    for (int k = 3; k >= 1; k--) {
+        if (k < nh && k > first) {
+            if (r.sp < TRACE_STACK) stack.push(r.sp++, val[k], key[k]);
+            else atomicOr(a.err, ERR_STACK);
         }
-        r.node = val[0];
-    } else {
-        r.node = pop_next(r, stack);
     }
-    park_leaves(r, stack);
+    // a directly entered leaf always waits behind the parked one; only a
+    // pop can bring a leaf to park
+    if (first < nh) r.node = first ? val[1] : val[0];
+    else advance(r, stack);
 }
 
 // Test the parked leaf, if any.
@@ -310,11 +321,7 @@ template <bool COUNT, class A>
 __device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint32_t& visits, uint32_t& tests) {
     const int leaf = r.leaf;
     if (leaf == WIDE_EMPTY) return;
-    if (++r.steps > 2u * (uint32_t)a.nt + 2u) {
-        atomicOr(a.err, ERR_STACK);
-        r.node = r.leaf = WIDE_EMPTY;
-        return;
-    }
+    r.steps++;
     if (COUNT) {
         visits++;
         tests++;
@@ -335,7 +342,10 @@ __device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint
         }
     }
     r.leaf = WIDE_EMPTY;
-    park_leaves(r, stack);
+    if (r.node != WIDE_EMPTY && r.node < 0) {
+        r.leaf = ~r.node;
+        advance(r, stack);
+    }
 }
 
 // One warp iteration of the two-phase traversal for every lane (active or
@@ -364,6 +374,7 @@ __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool
         if (COUNT) leaf_slots++;
         if (parked) leaf_step<COUNT>(a, r, stack, visits, tests);
     }
+    if (active) step_guard(a, r);
     return active && ray_done(r);
 }
 
