@@ -336,11 +336,11 @@ def run_gpu(args, rank, world):
         "tracer": {"node_visits_per_ray": round(visits_per_ray, 2), "tri_tests_per_ray": round(tests_per_ray, 2),
                    "flop_per_ray": round(flop_per_ray, 1),
                    # SIMT use of the traversal loop: lanes entering an internal
-                   # node per node step, lanes testing a triangle per leaf phase
+                   # node per node step, lanes testing a triangle per leaf round
                    "node_lanes_per_step": round(32 * (cnt["node_visits"] - cnt["tri_tests"])
                                                 / max(cnt["lane_slots"], 1), 2),
-                   "leaf_lanes_per_phase": round(32 * cnt["tri_tests"] / max(cnt["leaf_slots"], 1), 2),
-                   "leaf_phases_per_node_step": round(cnt["leaf_slots"] / max(cnt["lane_slots"], 1), 3)},
+                   "leaf_lanes_per_round": round(32 * cnt["tri_tests"] / max(cnt["leaf_slots"], 1), 2),
+                   "leaf_rounds_per_node_step": round(cnt["leaf_slots"] / max(cnt["lane_slots"], 1), 3)},
         "roofline": {"kernel": "k_trace", "bound": "alu",
                      "achieved": round(trace_tflops, 3) if trace_tflops else None,
                      "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",

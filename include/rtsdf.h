@@ -98,9 +98,10 @@ typedef struct {
        on (rtsdf_set_counting): rays cast, BVH nodes entered, ray/triangle
        tests (node_visits includes them); and the SIMT use of the traversal
        loop: lane slots (32 per warp and node step) of its node steps, and
-       lane slots (32 per warp) of its triangle phases.  Lanes busy per node
-       step = (node_visits - tri_tests) / lane_slots x 32, per triangle
-       phase = tri_tests / leaf_slots x 32. */
+       lane slots (32 per warp and round) of its triangle rounds (a triangle
+       phase runs one round, or two when enough lanes reach a second leaf).
+       Lanes busy per node step = (node_visits - tri_tests) / lane_slots x 32,
+       per triangle round = tri_tests / leaf_slots x 32. */
     int64_t rays, node_visits, tri_tests;
     int64_t lane_slots, leaf_slots;
 } rtsdf_stats;

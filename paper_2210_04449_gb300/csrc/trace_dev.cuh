@@ -93,21 +93,23 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 // Moller-Trumbore, closed triangle, t >= 0.  Returns hit; t and front out.
 __device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 v0, float3 e1, float3 e2, float& t,
                                        bool& front) {
+    // every quantity is computed (the same operations in the same order as
+    // a test with early exits), and the accept conditions are combined at
+    // the end: with the lanes of a warp on different triangles, the early
+    // exits would only add branches
     const float3 p = cross3(d, e2);
     const float det = dot3(e1, p);
-    if (det == 0.0f) return false;
     const float inv = __fdiv_rn(1.0f, det);
     const float3 tv = make_float3(__fsub_rn(o.x, v0.x), __fsub_rn(o.y, v0.y), __fsub_rn(o.z, v0.z));
     const float u = __fmul_rn(dot3(tv, p), inv);
-    if (!(u >= 0.0f && u <= 1.0f)) return false;
     const float3 q = cross3(tv, e1);
     const float v = __fmul_rn(dot3(d, q), inv);
-    if (!(v >= 0.0f && __fadd_rn(u, v) <= 1.0f)) return false;
     const float tt = __fmul_rn(dot3(e2, q), inv);
-    if (!(tt >= 0.0f)) return false;
+    const bool ok = (det != 0.0f) & (u >= 0.0f) & (u <= 1.0f) & (v >= 0.0f) & (__fadd_rn(u, v) <= 1.0f) &
+                    (tt >= 0.0f);
     t = tt;
     front = det > 0.0f;
-    return true;
+    return ok;
 }
 
 // Reciprocal of a direction component for the box tests only (an
@@ -357,7 +359,7 @@ __device__ __forceinline__ void leaf_step(const A& a, Ray& r, Stack& stack, uint
 constexpr int NODE_STEPS = 2;
 
 // COUNT: visits / tests count this lane's node visits and triangle tests,
-// leaf_slots the iterations in which the warp ran its leaf phase.
+// leaf_slots the leaf rounds the warp ran (one or two per leaf phase).
 template <bool COUNT, class A>
 __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool active, int leaf_min,
                                           uint32_t& visits, uint32_t& tests, uint32_t& leaf_slots) {
@@ -373,6 +375,14 @@ __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool
     if (pm && (__popc(pm) >= leaf_min || 2 * __popc(bm) >= leaf_min || im == 0)) {
         if (COUNT) leaf_slots++;
         if (parked) leaf_step<COUNT>(a, r, stack, visits, tests);
+        // a lane whose next node was a leaf waiting behind the tested one has
+        // parked it now: when enough lanes have, they test it in this phase
+        const bool again = parked && r.leaf != WIDE_EMPTY;
+        const unsigned am = __ballot_sync(0xFFFFFFFFu, again);
+        if (2 * __popc(am) >= leaf_min) {
+            if (COUNT) leaf_slots++;
+            if (again) leaf_step<COUNT>(a, r, stack, visits, tests);
+        }
     }
     if (active) step_guard(a, r);
     return active && ray_done(r);
