@@ -50,7 +50,7 @@ typedef enum {
     RTSDF_E_CUDA = 4,      /* CUDA runtime error (launch failure, sticky device error) */
     RTSDF_E_MESH = 5,      /* triangle index out of range, or a vertex not finite or
                               outside [bmin - extent/2, bmin + 3 extent/2]^3 */
-    RTSDF_E_OVERFLOW = 6,  /* a BVH traversal exceeded its fixed stack (result incomplete) */
+    RTSDF_E_OVERFLOW = 6,  /* a BVH traversal exceeded its fixed stack or its step bound (result incomplete) */
     RTSDF_E_TIMEOUT = 7    /* a bounded device-side wait expired (batched form) */
 } rtsdf_status;
 
@@ -168,6 +168,18 @@ rtsdf_status rtsdf_get_reset(rtsdf_t ctx, int32_t* on);
  * RTSDF_E_OOM, frees what it had allocated, and the hook turns itself off.
  * after < 0 turns it off.  Process-wide; for tests only. */
 void rtsdf_debug_fail_allocation(int64_t after);
+
+/* Test hook for the traversal's bounded-error path (not a step of the
+ * paper): rewrites the child ids of the context's root BVH node so that
+ * every non-empty child names the root itself -- a valid node index that
+ * closes a cycle.  A traversal that enters the cycle stops at its per-ray
+ * step bound (node and leaf steps <= 2 T + 2 for T triangles) or at its
+ * stack limit, with every memory access in bounds, and the next sync
+ * returns RTSDF_E_OVERFLOW.  A refit keeps the cycle (it keeps the
+ * topology); the next full rtsdf_build_bvh(ctx, 0) writes a valid tree.
+ * RTSDF_E_STATE without a built BVH over at least two triangles.  Waits for
+ * the context's stream.  For tests only. */
+rtsdf_status rtsdf_debug_bvh_cycle(rtsdf_t ctx);
 
 /* Builds (refit = 0) a binary BVH over the uploaded triangles, one triangle
  * per leaf, collapsed to 4-wide nodes for the tracer, or recomputes its

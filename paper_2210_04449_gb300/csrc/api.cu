@@ -664,6 +664,22 @@ rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
 
 void rtsdf_debug_fail_allocation(int64_t after) { g_fail_after.store(after < 0 ? -1 : (long long)after); }
 
+rtsdf_status rtsdf_debug_bvh_cycle(rtsdf_t c) {
+    if (!c) return RTSDF_E_ARG;
+    if (!c->bvh.built || c->bvh.n_wide < 1) return RTSDF_E_STATE;
+    // the root is wide node 0; its child ids are one int4
+    int4 ch;
+    cudaError_t e = cudaMemcpyAsync(&ch, &c->bvh.wide[0].child, sizeof(int4), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return from_cuda(e);
+    int* k = &ch.x;
+    for (int i = 0; i < 4; i++)
+        if (k[i] != WIDE_EMPTY) k[i] = 0;
+    e = cudaMemcpyAsync(&c->bvh.wide[0].child, &ch, sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? from_cuda(e) : RTSDF_OK;
+}
+
 rtsdf_status rtsdf_set_reset(rtsdf_t c, int32_t on) {
     if (!c || (on != 0 && on != 1)) return RTSDF_E_ARG;
     c->reset_on = on != 0;

@@ -1,8 +1,11 @@
 """Error behaviour of the C ABI with a GPU: bad meshes (E_MESH), calls out
-of order (E_STATE), bad arguments (E_ARG), and that a context is usable
-again after each.  Nothing here provokes a device fault: every error is a
-host-side argument check or a device validation word (bad indices are
-rewritten to 0 and bad vertices clamped before any kernel reads them)."""
+of order (E_STATE), bad arguments (E_ARG), a failed allocation (E_OOM), a
+cyclic tree stopped by the traversal's bounds (E_OVERFLOW), and that a
+context is usable again after each.  Nothing here provokes a device fault:
+every error is a host-side argument check or a device validation word (bad
+indices are rewritten to 0 and bad vertices clamped before any kernel reads
+them; the cyclic tree's node ids are valid indices, and every traversal
+loop and stack access is bounded)."""
 import numpy as np
 import pytest
 
@@ -155,3 +158,47 @@ def test_allocation_failure_returns_oom_and_recovers():
     assert np.array_equal(_fine_after_frame(rt, m), ref)
     rt.sync()
     rt.close()
+
+
+def test_cyclic_tree_reports_overflow_and_recovers():
+    # the root's children rewritten to name the root (valid node ids closing a
+    # cycle): every walk that enters it stops at its step bound or stack
+    # limit, the tracer and the exact-occlusion fallback report
+    # RTSDF_E_OVERFLOW, and a rebuilt tree plus the saved accumulation give
+    # the uninterrupted result bit for bit
+    import torch
+    from paper_2210_04449_gb300 import RTSDF, _abi
+    lib = _abi.lib()
+    m = S.tiny_scene()
+    ref = RTSDF(16, seed=1)
+    ref.upload_mesh(m.verts, m.tris)
+    ref.build_bvh()
+    for t in range(2):
+        ref.update(2.0, 8, t)
+    ref.sync()
+    want = {k: v.cpu().numpy().copy() for k, v in ref.grids().items() if k in ("accum", "counts", "fine")}
+    rt = RTSDF(16, seed=1)
+    assert _abi.STATUS_NAMES[lib.rtsdf_debug_bvh_cycle(rt._h)] == "RTSDF_E_STATE"   # no tree yet
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    rt.update(2.0, 8, 0)
+    rt.sync()
+    state = rt.save_state()
+    assert _abi.STATUS_NAMES[lib.rtsdf_debug_bvh_cycle(rt._h)] == "RTSDF_OK"
+    rt.update(2.0, 8, 1)
+    assert _name(rt.sync) == "RTSDF_E_OVERFLOW"
+    pos, nrm = S.floor_gbuffer(16, 16, y=0.05)
+    dev = torch.device("cuda")
+    blocked = torch.zeros(16 * 16, device=dev, dtype=torch.uint8)
+    rt.shadow_fallback(torch.tensor(pos, device=dev), torch.tensor(nrm, device=dev), (0.4, 1.0, 0.3), None,
+                       blocked=blocked)
+    assert _name(rt.sync) == "RTSDF_E_OVERFLOW"
+    rt.build_bvh()
+    rt.load_state(state)
+    rt.update(2.0, 8, 1)
+    rt.sync()
+    got = rt.grids()
+    for k, v in want.items():
+        assert np.array_equal(got[k].cpu().numpy(), v), k
+    rt.close()
+    ref.close()
