@@ -50,18 +50,18 @@ FLOP_PER_TEST = 30
 INST_PER_RAY = {
     # ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     # -k regex:k_trace -c 1 on "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant
-    # --no-configs" (1 pass; the first frame's launch, 393.68 ms): 372,087,739,161 warp instructions over
+    # --no-configs" (1 pass; the first frame's launch, 392.60 ms): 369,624,045,524 warp instructions over
     # 2,557,074 masked voxels x 8 texels x 64 rays = 1,309,221,888 rays
-    "6458408cee5695be": 284.21,
+    "bde58ef60a3ab05f": 282.32,
 }
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
 # by the sha256 of the sources it was measured on (the kernel and the BVH
 # builders, whose tree it walks); reported as null once any of them changes.
 TRAFFIC = {
-    # the same capture as INST_PER_RAY above (first k_trace<0> launch, SAH tree): 10.94 GB read +
-    # 175.41 MB written
-    "6458408cee5695be": 10.94e9 + 175.41e6,
+    # the same capture as INST_PER_RAY above (first k_trace<0> launch, SAH tree): 10.77 GB read +
+    # 175.59 MB written
+    "bde58ef60a3ab05f": 10.77e9 + 175.59e6,
 }
 TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 

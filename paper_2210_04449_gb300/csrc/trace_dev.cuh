@@ -376,10 +376,11 @@ __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool
         if (COUNT) leaf_slots++;
         if (parked) leaf_step<COUNT>(a, r, stack, visits, tests);
         // a lane whose next node was a leaf waiting behind the tested one has
-        // parked it now: when enough lanes have, they test it in this phase
+        // parked it now and tests it in a second round of this phase (any
+        // lane: measured slightly faster than waiting for several)
         const bool again = parked && r.leaf != WIDE_EMPTY;
         const unsigned am = __ballot_sync(0xFFFFFFFFu, again);
-        if (2 * __popc(am) >= leaf_min) {
+        if (am) {
             if (COUNT) leaf_slots++;
             if (again) leaf_step<COUNT>(a, r, stack, visits, tests);
         }
