@@ -50,18 +50,18 @@ FLOP_PER_TEST = 30
 INST_PER_RAY = {
     # ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     # -k regex:k_trace -c 1 on "bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-batch --no-variant
-    # --no-configs" (1 pass; the first frame's launch, 392.60 ms): 369,624,045,524 warp instructions over
+    # --no-configs" (1 pass; the first frame's launch, 374.85 ms): 372,760,948,333 warp instructions over
     # 2,557,074 masked voxels x 8 texels x 64 rays = 1,309,221,888 rays
-    "bde58ef60a3ab05f": 282.32,
+    "4585f2179a4ae7de": 284.72,
 }
 
 # DRAM bytes per launch of the tracer, from an ncu capture (profiles/), keyed
 # by the sha256 of the sources it was measured on (the kernel and the BVH
 # builders, whose tree it walks); reported as null once any of them changes.
 TRAFFIC = {
-    # the same capture as INST_PER_RAY above (first k_trace<0> launch, SAH tree): 10.77 GB read +
-    # 175.59 MB written
-    "bde58ef60a3ab05f": 10.77e9 + 175.59e6,
+    # the same capture as INST_PER_RAY above (first k_trace<0, 1> launch, SAH tree): 10.76 GB read +
+    # 174.75 MB written
+    "4585f2179a4ae7de": 10.76e9 + 174.75e6,
 }
 TRAFFIC_SOURCES = ("trace.cu", "trace_dev.cuh", "bvh.cu", "bvh_sah.cu")
 

@@ -181,6 +181,13 @@ void rtsdf_debug_fail_allocation(int64_t after);
  * the context's stream.  For tests only. */
 rtsdf_status rtsdf_debug_bvh_cycle(rtsdf_t ctx);
 
+/* Test switch for the tracers' node fetch (not a step of the paper): on
+ * (the default) the BVH traversal takes part of each node through the
+ * texture pipe when the node array fits a linear texture; off, every fetch
+ * is a plain load (the path for arrays beyond the texture width).  Both give
+ * the same results.  Process-wide, read at each launch; for tests only. */
+void rtsdf_debug_texture_fetch(int32_t on);
+
 /* Builds (refit = 0) a binary BVH over the uploaded triangles, one triangle
  * per leaf, collapsed to 4-wide nodes for the tracer, or recomputes its
  * boxes for the current vertex positions keeping the topology (refit = 1;

@@ -68,6 +68,7 @@ SIGNATURES = {
     "rtsdf_set_reset": (status_t, [ctx_t, c_i32]),
     "rtsdf_debug_fail_allocation": (None, [c_i64]),
     "rtsdf_debug_bvh_cycle": (status_t, [ctx_t]),
+    "rtsdf_debug_texture_fetch": (None, [c_i32]),
     "rtsdf_get_reset": (status_t, [ctx_t, ctypes.POINTER(c_i32)]),
     "rtsdf_build_bvh": (status_t, [ctx_t, c_int]),
     "rtsdf_voxelize": (status_t, [ctx_t]),

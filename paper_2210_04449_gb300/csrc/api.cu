@@ -65,6 +65,9 @@ __global__ void k_check_objects(const int32_t* vobj, int64_t nv, int n_obj, uint
 // -1 when off.
 std::atomic<long long> g_fail_after{-1};
 
+// Texture-path switch for tests (rtsdf_debug_texture_fetch), on by default.
+std::atomic<bool> g_texture_fetch{true};
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
     *p = nullptr;
@@ -91,6 +94,7 @@ void free_all(rtsdf_ctx* c) {
     dfree(c->accum); dfree(c->counts); dfree(c->fine); dfree(c->masked); dfree(c->d_masked_count);
     dfree(c->ray_min); dfree(c->ray_cnt); dfree(c->d_next_ray);
     dfree(c->bin_count); dfree(c->bin_start); dfree(c->bin_cursor); dfree(c->bin_items); dfree(c->bin_overflow);
+    drop_texture(c->bvh.wtex);
     dfree(c->bvh.nodes); dfree(c->bvh.wide); dfree(c->bvh.nbox); dfree(c->bvh.lbox); dfree(c->bvh.tri); dfree(c->bvh.leaf_tri); dfree(c->bvh.leaf_parent); dfree(c->bvh.flags);
     dfree(c->bvh.col_fb); dfree(c->bvh.col_fslot); dfree(c->bvh.col_nb); dfree(c->bvh.col_nslot);
     dfree(c->bvh.col_kids); dfree(c->bvh.col_nint); dfree(c->bvh.col_total);
@@ -187,6 +191,8 @@ rtsdf_status sync_status(rtsdf_ctx* c) {
 bool finite3(const float v[3]) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
 
 }  // namespace
+
+bool rtsdf::texture_fetch_on() { return g_texture_fetch.load(); }
 
 extern "C" {
 
@@ -663,6 +669,8 @@ rtsdf_status rtsdf_get_sign_mode(rtsdf_t c, int32_t* mode) {
 }
 
 void rtsdf_debug_fail_allocation(int64_t after) { g_fail_after.store(after < 0 ? -1 : (long long)after); }
+
+void rtsdf_debug_texture_fetch(int32_t on) { g_texture_fetch.store(on != 0); }
 
 rtsdf_status rtsdf_debug_bvh_cycle(rtsdf_t c) {
     if (!c) return RTSDF_E_ARG;

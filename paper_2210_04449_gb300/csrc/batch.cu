@@ -69,6 +69,7 @@ struct BatchParams {
 
 struct BvhRef {
     const WNode* wide;
+    cudaTextureObject_t wtex;   // the same nodes as int4 texels (used by the TEX trace)
     const float4* tri;
     long long nt;
     uint32_t* err;
@@ -247,6 +248,8 @@ __device__ __forceinline__ void batch_ray_prefix(const BatchArgs& b, unsigned lo
 
 // Stage 5: all scenes' rays from one dynamic counter (the per-scene
 // tracer's persistent-warp traversal; each lane remembers its ray's scene).
+// TEX: node fetches split between the load and texture pipes.
+template <bool TEX>
 __device__ __forceinline__ void batch_trace_rays(const BatchArgs& b, const unsigned long long* s_rp, int ns) {
     __shared__ int2 s_stack[SMEM_STACK][TRACE_THREADS];
     // per-warp chunk state, kept in shared memory (read only at refills) so
@@ -314,7 +317,7 @@ __device__ __forceinline__ void batch_trace_rays(const BatchArgs& b, const unsig
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         for (;;) {
-            const bool done = warp_step<false>(b.bvh, r, stk, active, b.leaf_min, dummy_v, dummy_t, dummy_l);
+            const bool done = warp_step<false, TEX>(b.bvh, r, stk, active, b.leaf_min, dummy_v, dummy_t, dummy_l);
             const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
             if (fin && done) {
                 const int scene = (int)s_scene[threadIdx.x];
@@ -501,7 +504,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
     unsigned long long* s_rp = s_prefix;
     __syncthreads();   // every thread is done with the voxel prefix
     batch_ray_prefix(b, s_rp, ns, P.rays);
-    batch_trace_rays(b, s_rp, ns);
+    batch_trace_rays<false>(b, s_rp, ns);
     if (!grid_barrier(b)) return;
     stamp(b, 6);
 
@@ -524,9 +527,10 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
 #define BATCH_TRACE_BLOCKS_PER_SM 8
 #endif
 
+template <bool TEX>
 __global__ void __launch_bounds__(TRACE_THREADS, BATCH_TRACE_BLOCKS_PER_SM) k_batch_trace(BatchArgs b) {
     if (*(volatile const uint32_t*)b.abort) return;
-    batch_trace_rays(b, b.ray_prefix, b.ns);
+    batch_trace_rays<TEX>(b, b.ray_prefix, b.ns);
 }
 
 __global__ void __launch_bounds__(256) k_batch_finalize(BatchArgs b) {
@@ -571,6 +575,7 @@ struct rtsdf_batch {
     int2* d_big = nullptr;
     int64_t big_cap = 0;
     WNode* d_wide_all = nullptr;     // all scenes' nodes
+    cudaTextureObject_t wtex_all = 0;  // d_wide_all as int4 texels (0: plain loads)
     float4* d_tri_all = nullptr;     // all scenes' leaf triangles
     int64_t wide_cap = 0, tri_cap = 0, total_nt = 0;
     uint32_t* d_ctr = nullptr;   // big_count, bar_count, bar_gen, abort, err
@@ -699,10 +704,12 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
     }
     // concatenated BVH of all scenes
     if (wo > b->wide_cap) {
+        drop_texture(b->wtex_all);   // the stream is idle (synchronised above)
         if (b->d_wide_all) cudaFree(b->d_wide_all);
         b->d_wide_all = nullptr;
         if ((e = cudaMalloc(&b->d_wide_all, sizeof(WNode) * (wo > 0 ? wo : 1)))) return e;
         b->wide_cap = wo;
+        b->wtex_all = make_int4_texture(b->d_wide_all, (sizeof(WNode) / 16) * (size_t)(wo > 0 ? wo : 1), b->device);
     }
     if (to > b->tri_cap) {
         if (b->d_tri_all) cudaFree(b->d_tri_all);
@@ -758,6 +765,7 @@ cudaError_t launch_frame_kernel(rtsdf_batch* b) {
     a.spins = b->barrier_spins > 0 ? (uint32_t)b->barrier_spins : BARRIER_SPINS;
     a.stamps = b->d_stamps;
     a.bvh.wide = b->d_wide_all;
+    a.bvh.wtex = texture_fetch_on() ? b->wtex_all : 0;
     a.bvh.tri = b->d_tri_all;
     a.bvh.nt = b->total_nt;
     a.bvh.err = b->d_ctr + 4;
@@ -770,7 +778,8 @@ cudaError_t launch_frame_kernel(rtsdf_batch* b) {
                                                 0, b->stream);
     if (e || !b->split_trace) return e;
     b->launches += 2;
-    k_batch_trace<<<b->trace_grid, TRACE_THREADS, 0, b->stream>>>(a);
+    if (a.bvh.wtex) k_batch_trace<true><<<b->trace_grid, TRACE_THREADS, 0, b->stream>>>(a);
+    else k_batch_trace<false><<<b->trace_grid, TRACE_THREADS, 0, b->stream>>>(a);
     k_batch_finalize<<<b->fin_grid, 256, 0, b->stream>>>(a);
     return cudaGetLastError();
 }
@@ -784,7 +793,9 @@ cudaError_t ensure_grid(rtsdf_batch* b) {
     const int use = (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) ? b->blocks_per_sm : per_sm;
     const unsigned g = (unsigned)(sms * use);
     int tper = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tper, k_batch_trace, TRACE_THREADS, 0);
+    if (b->wtex_all && texture_fetch_on())
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tper, k_batch_trace<true>, TRACE_THREADS, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tper, k_batch_trace<false>, TRACE_THREADS, 0);
     if (e) return e;
     if (tper < 1) return cudaErrorInvalidConfiguration;
     const unsigned tg = (unsigned)(sms * tper), fg = (unsigned)(sms * 8);
@@ -855,6 +866,7 @@ rtsdf_status rtsdf_batch_destroy(rtsdf_batch_t b) {
     if (b->d_vox_prefix) cudaFree(b->d_vox_prefix);
     if (b->d_tri_prefix) cudaFree(b->d_tri_prefix);
     if (b->d_big) cudaFree(b->d_big);
+    drop_texture(b->wtex_all);
     if (b->d_wide_all) cudaFree(b->d_wide_all);
     if (b->d_tri_all) cudaFree(b->d_tri_all);
     if (b->d_ctr) cudaFree(b->d_ctr);

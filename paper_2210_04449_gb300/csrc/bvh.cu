@@ -13,6 +13,7 @@
 //
 // Also here: the rigid per-object motion of animated scenes.
 #include <math_constants.h>
+#include <string.h>
 
 #include <utility>
 #include <vector>
@@ -529,11 +530,15 @@ static cudaError_t collapse_wide(rtsdf_ctx* c) {
         b.col_cap = cap;
     }
     if (b.wide_cap < cap) {
+        // the texture over the old array may still be in use by a launch
+        if ((e = cudaStreamSynchronize(c->stream))) return e;
+        drop_texture(b.wtex);
         if (b.wide) cudaFree(b.wide);
         b.wide = nullptr;
         b.wide_cap = 0;
         if ((e = cudaMalloc(&b.wide, sizeof(WNode) * cap))) return e;
         b.wide_cap = cap;
+        b.wtex = make_int4_texture(b.wide, (sizeof(WNode) / 16) * (size_t)cap, c->device);
     }
     int32_t *fb = b.col_fb, *fs = b.col_fslot, *nb = b.col_nb, *ns = b.col_nslot;
     RTSDF_LAUNCH(c, k_collapse_root, 1, 1, 0, b.root, fb, fs);
@@ -793,6 +798,33 @@ cudaError_t launch_transform(rtsdf_ctx* c) {
                      c->obj_xform);
     }
     return cudaGetLastError();
+}
+
+cudaTextureObject_t make_int4_texture(const void* ptr, size_t count, int device) {
+    int maxw = 0;
+    if (!ptr || count == 0 || cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, device) != cudaSuccess ||
+        count > (size_t)maxw)
+        return 0;
+    cudaResourceDesc rd;
+    memset(&rd, 0, sizeof(rd));
+    rd.resType = cudaResourceTypeLinear;
+    rd.res.linear.devPtr = const_cast<void*>(ptr);
+    rd.res.linear.desc = cudaCreateChannelDesc<int4>();
+    rd.res.linear.sizeInBytes = count * sizeof(int4);
+    cudaTextureDesc td;
+    memset(&td, 0, sizeof(td));
+    td.readMode = cudaReadModeElementType;
+    cudaTextureObject_t t = 0;
+    if (cudaCreateTextureObject(&t, &rd, &td, nullptr) != cudaSuccess) {
+        (void)cudaGetLastError();   // a failed creation leaves no error behind: plain loads serve
+        return 0;
+    }
+    return t;
+}
+
+void drop_texture(cudaTextureObject_t& t) {
+    if (t) cudaDestroyTextureObject(t);
+    t = 0;
 }
 
 }  // namespace rtsdf

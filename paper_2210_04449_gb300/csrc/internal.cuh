@@ -66,6 +66,7 @@ struct Bvh {
     int32_t* col_total = nullptr;
     int64_t col_cap = 0;
     int64_t n_wide = 0;
+    cudaTextureObject_t wtex = 0;  // the wide nodes as int4 texels (0: none; see make_int4_texture)
     float* nbox = nullptr;         // [nt - 1][6] box of every binary node
     float* lbox = nullptr;         // [nt][6] padded box of every leaf
     float4* tri = nullptr;         // [3 nt] per leaf: (v0, orig idx bits), (e1, 0), (e2, 0)
@@ -227,6 +228,14 @@ cudaError_t launch_voxelize(rtsdf_ctx* c);
 cudaError_t launch_jfa(rtsdf_ctx* c);
 cudaError_t launch_mask(rtsdf_ctx* c, float d_vox);
 cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame);
+// A texture object over `count` int4 texels at `ptr` (raw 32-bit words), or
+// 0 when the array exceeds the device's linear-texture width or creation
+// fails (the traversal then reads the nodes with plain loads).  drop_texture
+// destroys one; the caller makes sure no launch still uses it.
+cudaTextureObject_t make_int4_texture(const void* ptr, size_t count, int device);
+void drop_texture(cudaTextureObject_t& t);
+// Whether launches may take the texture path (rtsdf_debug_texture_fetch).
+bool texture_fetch_on();
 cudaError_t launch_bvh_build(rtsdf_ctx* c);
 cudaError_t launch_bvh_refit(rtsdf_ctx* c);
 cudaError_t launch_move(rtsdf_ctx* c);

@@ -304,6 +304,9 @@ ShadowArgs make_args(rtsdf_ctx* c, const float* sdf, const float* pos, const flo
 // origin fmaf(n, 2 eps, p) along L: a BVH traversal that stops at the first
 // hit (any hit decides), with the tracer's box and ray/triangle tests.  A
 // blocked point gets visibility 0; the others keep the march's value.
+// TEX: node fetches split between the load and texture pipes, as in the
+// tracer.
+template <bool TEX>
 __global__ void __launch_bounds__(dev::TRACE_THREADS) k_shadow_exact(dev::TraceArgs t, const float* __restrict__ pos,
                                                                      const float* __restrict__ nrm, long long npix,
                                                                      float Lx, float Ly, float Lz, float two_eps,
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(dev::TRACE_THREADS) k_shadow_exact(dev::TraceA
     // every step enters a node or tests a leaf (bounded by the step guard);
     // the loop ends at the first hit or when nothing is left
     while (r.bidx == 0x7FFFFFFF && !dev::ray_done(r)) {
-        dev::node_step<false>(t, r, stk, nv);
+        dev::node_step<false, TEX>(t, r, stk, nv);
         if (r.leaf != WIDE_EMPTY) dev::leaf_step<false>(t, r, stk, nv, ntest);
         dev::step_guard(t, r);
     }
@@ -375,11 +378,17 @@ cudaError_t launch_shadow_exact(rtsdf_ctx* c, const float* pos, const float* nrm
     dev::TraceArgs t;
     memset(&t, 0, sizeof(t));
     t.wide = c->bvh.wide;
+    t.wtex = texture_fetch_on() ? c->bvh.wtex : 0;
     t.tri = c->bvh.tri;
     t.nt = c->bvh.nt;
     t.err = c->d_err;
-    RTSDF_LAUNCH(c, k_shadow_exact, (unsigned)((npix + dev::TRACE_THREADS - 1) / dev::TRACE_THREADS),
-                 dev::TRACE_THREADS, 0, t, pos, nrm, (long long)npix, L[0], L[1], L[2], 2.f * eps, vis, blocked);
+    const unsigned g = (unsigned)((npix + dev::TRACE_THREADS - 1) / dev::TRACE_THREADS);
+    if (t.wtex)
+        RTSDF_LAUNCH(c, k_shadow_exact<true>, g, dev::TRACE_THREADS, 0, t, pos, nrm, (long long)npix, L[0], L[1],
+                     L[2], 2.f * eps, vis, blocked);
+    else
+        RTSDF_LAUNCH(c, k_shadow_exact<false>, g, dev::TRACE_THREADS, 0, t, pos, nrm, (long long)npix, L[0], L[1],
+                     L[2], 2.f * eps, vis, blocked);
     return cudaGetLastError();
 }
 

