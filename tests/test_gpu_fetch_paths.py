@@ -6,7 +6,9 @@ otherwise (arrays beyond the device's texture width).  The scenes here are
 small enough for textures, so the plain-load path is forced with the test
 switch rtsdf_debug_texture_fetch; the per-scene tracer (with object motion
 and the reset), the exact-occlusion fallback and the batched tracer (split
-launches) must give bit-identical outputs either way.
+launches) must give bit-identical outputs either way.  And the texture
+object follows a node array that grows: a context, or a batch, re-used with
+a larger mesh gives a fresh one's result.
 """
 import numpy as np
 import pytest
@@ -78,3 +80,78 @@ def test_texture_and_plain_node_fetch_agree():
     for i, (a, b) in enumerate(zip(tex_b, plain_b)):
         for k in a:
             assert np.array_equal(a[k], b[k]), (i, k)
+
+
+def test_node_texture_follows_a_growing_tree():
+    # a context that first builds a small tree and then a tree several times
+    # larger reallocates its node array; the texture object over it is
+    # replaced, and the frame equals a fresh context's bit for bit
+    from paper_2210_04449_gb300 import RTSDF
+    small = S.tiny_scene()
+    big = S.animated_scene(3, n_objects=25, n_lon=16, n_lat=9)
+
+    def frame(rt, mesh):
+        rt.upload_mesh(mesh.verts, mesh.tris)
+        rt.build_bvh()
+        rt.update(2.0, 16, 0)
+        rt.sync()
+        return {k: v.cpu().numpy().copy() for k, v in rt.grids().items() if k in ("accum", "counts", "fine")}
+
+    rt = RTSDF(32, beta_vox=0.5, seed=4)
+    frame(rt, small)
+    rt.load_state(_fresh_state(32))
+    got = frame(rt, big)
+    rt.close()
+    ref = RTSDF(32, beta_vox=0.5, seed=4)
+    want = frame(ref, big)
+    ref.close()
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+
+
+def _fresh_state(n):
+    from paper_2210_04449_gb300 import RTSDF
+    rt = RTSDF(n, beta_vox=0.5, seed=4)
+    s = rt.save_state()
+    rt.close()
+    return s
+
+
+def test_batch_node_texture_follows_a_growing_tree():
+    # the batch's concatenated node array (and its texture) grows when a
+    # scene's mesh does; the frame equals a fresh batch's
+    from paper_2210_04449_gb300 import RTSDFBatch
+    cfgs = [dict(coarse_n=24, beta_vox=0.5, seed=5), dict(coarse_n=32, beta_vox=0.5, seed=6)]
+    small = S.tiny_scene()
+    big = S.animated_scene(4, n_objects=20, n_lon=16, n_lat=9)
+
+    def run(b, meshes, frame):
+        for sc, m in zip(b.scenes, meshes):
+            sc.upload_mesh(m.verts, m.tris)
+            sc.build_bvh()
+        b.frame(2.0, 16, frame)
+        b.sync()
+        return [{k: sc.grids()[k].cpu().numpy().copy() for k in ("accum", "counts", "fine")} for sc in b.scenes]
+
+    b = RTSDFBatch(cfgs)
+    b.set_tuning(split_trace=1)
+    run(b, [small, small], 0)
+    for sc in b.scenes:
+        sc.load_state(_fresh_state_of(sc))
+    got = run(b, [big, small], 0)
+    b.close()
+    f = RTSDFBatch(cfgs)
+    f.set_tuning(split_trace=1)
+    want = run(f, [big, small], 0)
+    f.close()
+    for i, (a, w) in enumerate(zip(got, want)):
+        for k in w:
+            assert np.array_equal(a[k], w[k]), (i, k)
+
+
+def _fresh_state_of(sc):
+    from paper_2210_04449_gb300 import RTSDF
+    rt = RTSDF(sc.coarse_n, beta_vox=0.5, seed=0)
+    s = rt.save_state()
+    rt.close()
+    return s
