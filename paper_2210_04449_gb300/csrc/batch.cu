@@ -96,6 +96,9 @@ struct BatchArgs {
     unsigned long long* stamps;   // [8] global timer at the stage boundaries (block 0)
     BvhRef bvh;               // every scene's BVH in one array (child ids rebased)
     int split;                // 1: trace and finalize run as two launches after the pipeline launch
+    int phase;                // split form: 1 = stages 0-2 (the jump flood follows as launches of its
+                              // own), 2 = stage 4 on; 0 = the whole frame in one launch
+    const uint32_t* jfa_blocks;   // split jump flood: [max_passes][ns + 1] prefix over scenes of their blocks
     unsigned long long* ray_prefix;   // [ns + 1] split form: ray prefix over scenes, written after the mask
     uint32_t* fin_done;       // split finalize: blocks done (the last one stamps the frame's end)
 };
@@ -232,6 +235,41 @@ __device__ __noinline__ void batch_jfa_pass(const BatchArgs& b, const unsigned l
     }
 }
 
+// Split form of stage 3: jump-flood pass p of every scene that has one as
+// one launch of the per-scene z-blocked pass (dev::jfa_zblock_column, T = 8)
+// over all scenes' columns: blocks of 32 x 4 threads, a scene's blocks
+// consecutive (jfa_blocks row p: prefix over scenes of their block counts,
+// 0 for a scene without pass p).  Inside the pipeline launch the pass would
+// have that launch's register budget, which rules out the register-blocked
+// columns.  Skips its work when the pipeline launch gave up at a barrier.
+__global__ void __launch_bounds__(128, 4) k_batch_jfa(BatchArgs b, int p) {
+    if (*(volatile const uint32_t*)b.abort) return;
+    const uint32_t* pre = b.jfa_blocks + (size_t)p * (size_t)(b.ns + 1);
+    const uint32_t blk = blockIdx.x;
+    int lo = 0, hi = b.ns - 1;   // largest s with pre[s] <= blk (a scene without blocks is skipped)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const SceneDesc& d = b.sc[lo];
+    const int n = d.t.nc, L = d.passes;
+    const int k = 1 << (L - 1 - p);
+    const uint32_t nbx = ((uint32_t)n + 31u) / 32u, nby = ((uint32_t)n + 3u) / 4u;
+    uint32_t local = blk - pre[lo];
+    const uint32_t bx = local % nbx;
+    local /= nbx;
+    const uint32_t by = local % nby, bz = local / nby;
+    const int x = (int)(bx * 32u + threadIdx.x), y = (int)(by * 4u + threadIdx.y);
+    if (x >= n || y >= n) return;
+    const int rz = (int)(bz % (uint32_t)k), g = (int)(bz / (uint32_t)k);
+    const uint32_t* in = d.seeds[p & 1];
+    uint32_t* out = d.seeds[(p + 1) & 1];
+    float* coarse = const_cast<float*>(d.t.coarse);
+    if (p == L - 1) dev::jfa_zblock_column<true, 8>(in, out, n, k, x, y, rz, g, coarse, d.hc, d.beta_h);
+    else dev::jfa_zblock_column<false, 8>(in, out, n, k, x, y, rz, g, coarse, d.hc, d.beta_h);
+}
+
 // Ray prefix over scenes (8 texel slots per masked voxel, `rays` rays
 // each), in shared memory; every thread of the block returns with it.
 __device__ __forceinline__ void batch_ray_prefix(const BatchArgs& b, unsigned long long* s_rp, int ns, int rays) {
@@ -363,51 +401,54 @@ __global__ void __launch_bounds__(TRACE_THREADS, BATCH_BLOCKS_PER_SM) k_batch_fr
     // would stay allocated through the trace stage
     __shared__ BatchParams P;
     const int ns = b.ns;
-    stamp(b, 0);
+    if (b.phase != 2) stamp(b, 0);
     // prefix over scenes: voxels in stages 0-4, rays in stages 5-6
     __shared__ unsigned long long s_prefix[MAX_BATCH + 1];
     unsigned long long* s_vp = s_prefix;
     if (threadIdx.x == 0) P = *b.params;
     for (int i = threadIdx.x; i <= ns; i += blockDim.x) s_vp[i] = b.vox_prefix[i];
     __syncthreads();
-
-    // ---- stage 0: clear the seed grids and the per-scene counters
-    for (int s = 0; s < ns; s++) {
-        const uint64_t n3 = s_vp[s + 1] - s_vp[s];
-        uint32_t* sd = b.sc[s].seeds[0];
-        for (uint64_t g = tid; g < n3; g += nthr) sd[g] = SEED_EMPTY;
-    }
-    for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) {
-        // the frame's ray parameters go into each scene's tracer fields, so
-        // that the trace stage reads them in place (no copy of the fields)
-        TraceArgs& t = const_cast<SceneDesc&>(b.sc[s]).t;
-        *const_cast<uint32_t*>(t.count) = 0u;
-        t.rays = P.rays;
-        t.log2_rays = P.log2_rays;
-        t.frame = P.frame;
-    }
-    if (tid == 0) {
-        *b.big_count = 0u;
-        *b.next_ray = 0ull;
-    }
-    if (!grid_barrier(b)) return;
-    stamp(b, 1);
-
-    // ---- stage 1: voxelize (small triangles inline, large ones listed)
-    batch_voxelize_small(b, tid, nthr);
-    if (!grid_barrier(b)) return;
-    stamp(b, 2);
-
-    // ---- stage 2: large triangles, one block each
-    batch_voxelize_big(b);
-    if (!grid_barrier(b)) return;
-    stamp(b, 3);
-
-    // ---- stage 3: jump flooding, pass p of every scene that has one
-    for (int p = 0; p < b.max_passes; p++) {
-        batch_jfa_pass(b, s_vp, ns, p, tid, nthr);
+    if (b.phase == 2 && *(volatile const uint32_t*)b.abort) return;
+    if (b.phase != 2) {   // stages 0-3 (phase 2 starts after the flood launches)
+        // ---- stage 0: clear the seed grids and the per-scene counters
+        for (int s = 0; s < ns; s++) {
+            const uint64_t n3 = s_vp[s + 1] - s_vp[s];
+            uint32_t* sd = b.sc[s].seeds[0];
+            for (uint64_t g = tid; g < n3; g += nthr) sd[g] = SEED_EMPTY;
+        }
+        for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) {
+            // the frame's ray parameters go into each scene's tracer fields, so
+            // that the trace stage reads them in place (no copy of the fields)
+            TraceArgs& t = const_cast<SceneDesc&>(b.sc[s]).t;
+            *const_cast<uint32_t*>(t.count) = 0u;
+            t.rays = P.rays;
+            t.log2_rays = P.log2_rays;
+            t.frame = P.frame;
+        }
+        if (tid == 0) {
+            *b.big_count = 0u;
+            *b.next_ray = 0ull;
+        }
         if (!grid_barrier(b)) return;
-    }
+        stamp(b, 1);
+
+        // ---- stage 1: voxelize (small triangles inline, large ones listed)
+        batch_voxelize_small(b, tid, nthr);
+        if (!grid_barrier(b)) return;
+        stamp(b, 2);
+
+        // ---- stage 2: large triangles, one block each
+        batch_voxelize_big(b);
+        if (!grid_barrier(b)) return;
+        stamp(b, 3);
+        if (b.phase == 1) return;   // the jump flood follows as launches of its own (k_batch_jfa)
+
+        // ---- stage 3: jump flooding, pass p of every scene that has one
+        for (int p = 0; p < b.max_passes; p++) {
+            batch_jfa_pass(b, s_vp, ns, p, tid, nthr);
+            if (!grid_barrier(b)) return;
+        }
+    }   // stages 0-3
     // scenes without jump steps (N = 1): coarse value straight from the seed
     for (uint64_t s = tid; s < (uint64_t)ns; s += nthr) {
         const SceneDesc& d = b.sc[s];
@@ -591,6 +632,9 @@ struct rtsdf_batch {
     unsigned trace_grid = 0;     // blocks of the split trace launch
     unsigned fin_grid = 0;       // blocks of the split finalize launch
     unsigned long long* d_ray_prefix = nullptr;   // [MAX_BATCH + 1]
+    uint32_t* d_jfa_blocks = nullptr;   // split jump flood: [max_passes][ns + 1] block prefix per pass
+    size_t jfa_cap = 0;                 // entries of d_jfa_blocks
+    std::vector<uint32_t> jfa_total;    // blocks of each pass's launch
     int refill_min = 12;
     int ray_chunk = 1024;
     int leaf_min = 12;
@@ -738,6 +782,37 @@ cudaError_t refresh_tables(rtsdf_batch* b, bool* changed) {
         return e;
     if ((e = cudaMemcpy(b->d_tri_prefix, tp.data(), sizeof(unsigned long long) * (ns + 1), cudaMemcpyHostToDevice)))
         return e;
+    // split jump flood: per pass, the z-blocked pass's blocks of every
+    // scene that has the pass (32 x 4 columns of T = 8 lattice voxels)
+    {
+        const size_t rows = (size_t)maxp, cols = (size_t)ns + 1;
+        std::vector<uint32_t> pre(rows * cols, 0u);
+        b->jfa_total.assign(rows, 0u);
+        for (int p = 0; p < maxp; p++) {
+            uint64_t acc = 0;
+            for (int s = 0; s < ns; s++) {
+                pre[(size_t)p * cols + s] = (uint32_t)acc;
+                const int L = desc[s].passes, n = desc[s].t.nc;
+                if (p < L) {
+                    const uint64_t k = 1ull << (L - 1 - p), lat = ((uint64_t)n + k - 1) / k;
+                    acc += (uint64_t)((n + 31) / 32) * (uint64_t)((n + 3) / 4) * ((lat + 7) / 8) * k;
+                }
+            }
+            if (acc > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+            pre[(size_t)p * cols + ns] = (uint32_t)acc;
+            b->jfa_total[p] = (uint32_t)acc;
+        }
+        if (rows * cols > b->jfa_cap) {
+            if (b->d_jfa_blocks) cudaFree(b->d_jfa_blocks);
+            b->d_jfa_blocks = nullptr;
+            b->jfa_cap = 0;
+            if ((e = cudaMalloc(&b->d_jfa_blocks, sizeof(uint32_t) * rows * cols))) return e;
+            b->jfa_cap = rows * cols;
+        }
+        if (rows > 0 &&
+            (e = cudaMemcpy(b->d_jfa_blocks, pre.data(), sizeof(uint32_t) * rows * cols, cudaMemcpyHostToDevice)))
+            return e;
+    }
     b->h_desc = desc;
     b->max_passes = maxp;
     *changed = true;
@@ -772,11 +847,26 @@ cudaError_t launch_frame_kernel(rtsdf_batch* b) {
     a.split = b->split_trace;
     a.ray_prefix = b->d_ray_prefix;
     a.fin_done = b->d_ctr + 5;
+    a.jfa_blocks = b->d_jfa_blocks;
+    a.phase = b->split_trace ? 1 : 0;
     void* args[] = {&a};
     b->launches++;
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_batch_frame, dim3(b->grid), dim3(TRACE_THREADS), args,
                                                 0, b->stream);
     if (e || !b->split_trace) return e;
+    // split form: the jump flood as one launch per pass, the rest of the
+    // pipeline (mask, ray prefix) as a second cooperative launch, then the
+    // trace and the finalize
+    for (int p = 0; p < b->max_passes; p++) {
+        if (b->jfa_total[p] == 0) continue;
+        k_batch_jfa<<<b->jfa_total[p], dim3(32, 4, 1), 0, b->stream>>>(a, p);
+        b->launches++;
+    }
+    a.phase = 2;
+    b->launches++;
+    e = cudaLaunchCooperativeKernel((const void*)k_batch_frame, dim3(b->grid), dim3(TRACE_THREADS), args, 0,
+                                    b->stream);
+    if (e) return e;
     b->launches += 2;
     if (a.bvh.wtex) k_batch_trace<true><<<b->trace_grid, TRACE_THREADS, 0, b->stream>>>(a);
     else k_batch_trace<false><<<b->trace_grid, TRACE_THREADS, 0, b->stream>>>(a);
@@ -873,6 +963,7 @@ rtsdf_status rtsdf_batch_destroy(rtsdf_batch_t b) {
     if (b->d_next_ray) cudaFree(b->d_next_ray);
     if (b->d_stamps) cudaFree(b->d_stamps);
     if (b->d_ray_prefix) cudaFree(b->d_ray_prefix);
+    if (b->d_jfa_blocks) cudaFree(b->d_jfa_blocks);
     if (b->d_params) cudaFree(b->d_params);
     if (b->h_params) cudaFreeHost(b->h_params);
     if (b->ev0) cudaEventDestroy(b->ev0);

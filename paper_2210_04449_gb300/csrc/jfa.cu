@@ -51,37 +51,8 @@ void launch_pass(rtsdf_ctx* c, const uint32_t* in, uint32_t* out, int n, int k, 
     else RTSDF_LAUNCH(c, (k_jfa_pass<false, TX, TY>), grid, block, 0, in, out, n, k, c->coarse, c->hc, beta_h);
 }
 
-// z-blocked pass: a thread floods T voxels of one z-lattice column,
-// (x, y, z_t = rz + k (T g + t)) for t < T; blocks are 32 x 4 threads in
-// (x, y), blockIdx.z = g k + rz.  The T + 2 candidate z-slices (9 voxels
-// each) are read once and shared by the column's voxels.
-//
-// Per candidate seed s = (sx, sy, sz, 0) of a slice, once:
-//   A = (sx - x)^2 + (sy - y)^2 + sz^2            vabsdiff4 + dp4a, whose
-//       accumulator adds s's top byte (as 0x7F000000): a seedless candidate
-//       (all ones) lands above every real key
-// Per voxel z_t and candidate, one instruction:
-//   key = A - 2 z_t sz = D2 - z_t^2               dp2a.hi (16-bit -2 z_t times byte 2)
-// Keys of one voxel share the z_t^2 offset, so their order is D2's; the
-// arg-min is the smallest key (three-input signed minima), then the smallest
-// seed among the candidates at that key (one clamped add-min and one
-// multiply-add per candidate, then unsigned minima) -- the lexicographic
-// (D2, seed) minimum.  An x or y offset that leaves the grid reads the voxel's own
-// coordinate on that axis (a duplicate of another candidate); a z-slice
-// outside the grid holds no seed.  Slices roll through registers: voxel t
-// needs slices t .. t + 2 only.
-__device__ __forceinline__ int dp2a_hi_s_u(uint32_t a, uint32_t b, int c) {
-    int d;
-    asm("dp2a.hi.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-
-__device__ __forceinline__ int vimin3_s(int a, int b, int c) { return __vimin3_s32(a, b, c); }
-
-// the smallest key a seedless candidate can have: A >= 0x7F000000, minus
-// 2 z sz with z, sz <= 255
-constexpr int SEEDLESS_KEY_MIN = 0x7F000000 - 2 * 255 * 255;
-
+// z-blocked pass (dev::jfa_zblock_column): blocks of 32 x 4 threads in
+// (x, y), blockIdx.z = g k + rz.
 template <bool FINAL, int T>
 __global__ void __launch_bounds__(128, 4) k_jfa_zblock(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                                       int n, int k, float* __restrict__ coarse, float hc,
@@ -90,78 +61,7 @@ __global__ void __launch_bounds__(128, 4) k_jfa_zblock(const uint32_t* __restric
     const int y = blockIdx.y * 4 + threadIdx.y;
     const int rz = (int)(blockIdx.z % (unsigned)k), g = (int)(blockIdx.z / (unsigned)k);
     if (x >= n || y >= n) return;
-    const uint32_t n2 = (uint32_t)n * (uint32_t)n;
-    uint32_t xs[3], ys[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const int o = (i - 1) * k;
-        xs[i] = (uint32_t)((x + o >= 0 && x + o < n) ? x + o : x);
-        ys[i] = (uint32_t)((y + o >= 0 && y + o < n) ? y + o : y) * (uint32_t)n;
-    }
-    const uint32_t vxy = (uint32_t)x | ((uint32_t)y << 8);
-    // slice j (0 .. T + 1) holds z-lattice index T g + j - 1
-    uint32_t ss[T + 2][9];
-    int aa[T + 2][9];
-    auto load_slice = [&](int j) {
-        const int z = rz + k * (T * g + j - 1);
-        if (z >= 0 && z < n) {
-            const uint32_t zo = (uint32_t)z * n2;
-#pragma unroll
-            for (int iy = 0; iy < 3; iy++)
-#pragma unroll
-                for (int ix = 0; ix < 3; ix++) {
-                    const uint32_t sv = __ldg(in + zo + ys[iy] + xs[ix]);
-                    const uint32_t d = __vabsdiffu4(sv, vxy);
-                    ss[j][3 * iy + ix] = sv;
-                    aa[j][3 * iy + ix] = (int)__dp4a(d, d, sv & 0x7F000000u);
-                }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 9; c++) {
-                ss[j][c] = SEED_EMPTY;
-                aa[j][c] = 0x7F000000;
-            }
-        }
-    };
-    load_slice(0);
-    load_slice(1);
-#pragma unroll
-    for (int t = 0; t < T; t++) {
-        load_slice(t + 2);
-        const int z = rz + k * (T * g + t);
-        if (z >= n) break;
-        // 16-bit -2 z in the low half, 0 in the high half (byte 3 is 0 or, for
-        // a seedless candidate, already pushed out of range through A)
-        const uint32_t wz = (uint32_t)(-2 * z) & 0xFFFFu;
-        int key[27];
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-#pragma unroll
-            for (int c = 0; c < 9; c++) key[9 * j + c] = dp2a_hi_s_u(wz, ss[t + j][c], aa[t + j][c]);
-        int kmin = vimin3_s(key[0], key[1], key[2]);
-#pragma unroll
-        for (int c = 3; c < 27; c += 2) kmin = vimin3_s(kmin, key[c], key[c + 1]);
-        // smallest seed among the candidates at kmin: gap = min(key - kmin,
-        // 255) is 0 exactly for them, and gap * 2^24 + seed then orders every
-        // such candidate (a real seed, < 2^24) before every other one (>= 2^24;
-        // a seedless one has gap 255 and wraps to 254 * 2^24 + 0xFFFFFF).
-        // When kmin itself is a seedless key, every candidate is seedless.
-        uint32_t v[27];
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-#pragma unroll
-            for (int c = 0; c < 9; c++) {
-                const uint32_t gap = (uint32_t)__viaddmin_s32(key[9 * j + c], -kmin, 255);
-                v[9 * j + c] = gap * 0x01000000u + ss[t + j][c];
-            }
-        uint32_t vmin = __vimin3_u32(v[0], v[1], v[2]);
-#pragma unroll
-        for (int c = 3; c < 27; c += 2) vmin = __vimin3_u32(vmin, v[c], v[c + 1]);
-        const uint32_t best = kmin >= SEEDLESS_KEY_MIN ? SEED_EMPTY : vmin;
-        const uint32_t idx = (uint32_t)x + ys[1] + (uint32_t)z * n2;
-        out[idx] = best;
-        if (FINAL) coarse[idx] = dev::coarse_value(best, (uint32_t)(kmin + z * z), hc, beta_h);
-    }
+    dev::jfa_zblock_column<FINAL, T>(in, out, n, k, x, y, rz, g, coarse, hc, beta_h);
 }
 
 template <int T>
