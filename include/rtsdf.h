@@ -114,7 +114,9 @@ rtsdf_status rtsdf_create(const rtsdf_config* cfg, rtsdf_t* out);
 /* Frees every device buffer of the context (synchronises its stream first). */
 rtsdf_status rtsdf_destroy(rtsdf_t ctx);
 
-/* Changes the stream later calls enqueue on. */
+/* Changes the stream later calls enqueue on.  Waits first for the work
+ * already enqueued on the previous stream (RTSDF_E_CUDA if that work
+ * failed), so later calls are ordered after it. */
 rtsdf_status rtsdf_set_stream(rtsdf_t ctx, void* stream);
 
 /* Sec. 2.1 input: copy a triangle mesh into the context.  verts: float32

@@ -275,6 +275,14 @@ rtsdf_status rtsdf_destroy(rtsdf_t c) {
 
 rtsdf_status rtsdf_set_stream(rtsdf_t c, void* stream) {
     if (!c) return RTSDF_E_ARG;
+    // work already enqueued on the old stream finishes first, so that later
+    // calls on the new one are ordered after it (and no buffer or texture
+    // object is released while that work may still use it)
+    if ((cudaStream_t)stream != c->stream) {
+        DeviceGuard g(c->device);
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     c->stream = (cudaStream_t)stream;
     c->cfg.stream = stream;
     return RTSDF_OK;

@@ -202,3 +202,32 @@ def test_cyclic_tree_reports_overflow_and_recovers():
         assert np.array_equal(got[k].cpu().numpy(), v), k
     rt.close()
     ref.close()
+
+
+def test_stream_switch_orders_later_calls():
+    # frames alternate between two streams; rtsdf_set_stream waits for the
+    # old stream, so the result equals a context that stays on one stream
+    import torch
+    from paper_2210_04449_gb300 import RTSDF
+    m = S.animated_scene(2, n_objects=12, n_lon=16, n_lat=9)
+    ref = RTSDF(32, seed=3)
+    want = None
+    for t in range(3):
+        if t == 0:
+            ref.upload_mesh(m.verts, m.tris)
+            ref.build_bvh()
+        ref.update(2.0, 16, t)
+    ref.sync()
+    want = ref.grids()["fine"].cpu().numpy().copy()
+    ref.close()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    rt = RTSDF(32, seed=3)
+    rt.set_stream(streams[0])
+    rt.upload_mesh(m.verts, m.tris)
+    rt.build_bvh()
+    for t in range(3):
+        rt.set_stream(streams[t % 2])
+        rt.update(2.0, 16, t)
+    rt.sync()
+    assert np.array_equal(rt.grids()["fine"].cpu().numpy(), want)
+    rt.close()
